@@ -1,0 +1,174 @@
+/* deg.h -- C ABI of libdeg: batched Dynamic Exploration Graph (DEG) search on one GB300.
+ *
+ * The paper (arXiv 2307.10479) defines the method:
+ *   - Alg. 1 RangeSearch(G, S, q, k, eps) (Sec. 2.1)      -> deg_search / deg_explore
+ *   - exploration queries seeded at the query's own vertex (Sec. 5.7) -> deg_explore
+ *   - Eq. 1, the exact k nearest neighbours                -> knn_exact
+ *   - Sec. 4 construction (Alg. 2-5)                       -> deg_build (host, not the GPU path)
+ *   - Sec. 4.4: search graphs drop edge weights and start at the "median vertex"
+ *                                                          -> deg_upload / deg_entry_vertex
+ *
+ * Conventions for every call:
+ *   - Distances are Euclidean (L2, not squared). Result lists are sorted ascending by
+ *     (distance, id), ties going to the lower id; a list shorter than k is padded with
+ *     id -1 and distance +inf.
+ *   - Pointers named *_dev are device pointers (cudaMalloc'd or torch tensors); *_host are
+ *     host pointers. The caller owns every buffer it passes; the library owns a deg_index and
+ *     the device copies it makes. `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Device work is asynchronous on `stream`: the return value reports argument validation
+ *     and launch errors only. Per-query outcomes go to the optional status_dev array.
+ *   - On failure a call returns a negative deg_status, leaves outputs unspecified and records
+ *     a message for deg_last_error() (thread-local).
+ *   - Searches on one index may run concurrently on different streams only when each passes
+ *     its own `workspace` (deg_search_ex); the convenience calls share the index's workspace
+ *     and must be ordered by the caller (same stream or explicit synchronisation).
+ */
+#ifndef DEG_H
+#define DEG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DEG_API __attribute__((visibility("default")))
+#else
+#define DEG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEG_OK = 0,
+    DEG_EINVAL = -1,      /* invalid argument (k < 1, eps < 0 or NaN, ids out of range, ...) */
+    DEG_ENOMEM = -2,      /* host or device allocation failed                                */
+    DEG_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed                     */
+    DEG_EIO = -4,         /* file could not be read or written, or has a bad format          */
+    DEG_EOVERFLOW = -5,   /* per query: a bounded structure overflowed (result not exact)    */
+    DEG_EHOPLIMIT = -6,   /* per query: stopped at deg_search_params.max_hops expansions     */
+    DEG_ETIMEOUT = -7,    /* a bounded device wait expired                                   */
+    DEG_EGRAPH = -8,      /* graph violates a DEG invariant (degree, symmetry, loops)        */
+    DEG_ENOTREADY = -9    /* index not uploaded to the device (call deg_upload first)        */
+} deg_status;
+
+typedef enum {
+    DEG_F32 = 0,          /* rows stored as float32                                          */
+    DEG_BF16 = 1,         /* rows stored as bfloat16 (round to nearest even), no scale       */
+    DEG_FP8 = 2           /* rows stored as FP8 E4M3 codes with a per-row float32 scale      */
+} deg_precision;
+
+/* Construction parameters (paper Table 2): even degree d >= 4; k_ext >= d and eps_ext for the
+ * search of a new vertex (Alg. 3); k_opt, eps_opt, i_opt for edge optimisation (Alg. 4);
+ * refine_rounds calls of Alg. 5 after the last insertion, drawing vertices from `seed`. */
+typedef struct {
+    int32_t degree;
+    int32_t k_ext;
+    float eps_ext;
+    int32_t k_opt;
+    float eps_opt;
+    int32_t i_opt;
+    int32_t refine_rounds;
+    uint64_t seed;
+} deg_build_params;
+
+typedef struct deg_index deg_index;   /* opaque, owned by the library */
+
+/* ---- index lifecycle ------------------------------------------------------------------- */
+
+/* Build a DEG over base_host [n][dim] float32 on the host (paper Sec. 4.2-4.3, Alg. 2-5).
+ * Copies the vectors. n >= degree + 1. Single-threaded; minutes to hours at n = 10^6.
+ * progress (nullable) receives the number of vertices inserted so far. */
+DEG_API deg_status deg_build(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
+                     volatile int64_t* progress, deg_index** out);
+
+/* Wrap an existing graph: base_host [n][dim] float32 and adj_host [n][degree] int32 are copied.
+ * The adjacency is checked (every entry in [0,n), no self-loops, no duplicates, symmetric,
+ * degree even and >= 4): DEG_EGRAPH if it is not a valid undirected regular graph. */
+DEG_API deg_status deg_index_from_arrays(const float* base_host, const int32_t* adj_host, int64_t n,
+                                 int32_t dim, int32_t degree, deg_index** out);
+
+/* Graph file: header, adjacency [n][degree] int32 and, if with_vectors, the vectors. Edge
+ * weights are not stored (Sec. 4.4: search drops them; they are recomputed when needed).
+ * A file without vectors carries a checksum of them; deg_load then requires base_host
+ * (otherwise ignored, may be NULL) and fails with DEG_EIO if the checksum differs. */
+DEG_API deg_status deg_save(const deg_index* idx, const char* path, int32_t with_vectors);
+DEG_API deg_status deg_load(const char* path, const float* base_host, deg_index** out);
+
+/* Shape queries; deg_get_adjacency copies the graph out to adj_host [n][degree]. */
+DEG_API deg_status deg_index_info(const deg_index* idx, int64_t* n, int32_t* dim, int32_t* degree);
+DEG_API deg_status deg_get_adjacency(const deg_index* idx, int32_t* adj_host);
+
+/* Make the index resident on the current CUDA device: float32 rows (always, padded to a
+ * multiple of 4 floats), the adjacency, and the reduced-precision copies named in
+ * precision_mask (bit 1 << DEG_BF16, bit 1 << DEG_FP8). Computes the fixed entry vertex on the
+ * device: the row nearest to the per-coordinate lower median (rank floor((n-1)/2)) of all rows
+ * -- the paper's "median vertex" (Sec. 4.4). Synchronises `stream` before returning. */
+DEG_API deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* stream);
+
+/* The entry vertex computed by deg_upload, or -1 before it. */
+DEG_API int32_t deg_entry_vertex(const deg_index* idx);
+
+/* Release every host and device resource of the index (NULL is a no-op). */
+DEG_API void deg_free(deg_index* idx);
+
+/* ---- search (Alg. 1) ---------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t k;            /* results per query, 1 <= k <= 1024 and k <= n (k <= n-1 to explore) */
+    float eps;            /* range factor eps >= 0 of Alg. 1                                  */
+    int32_t precision;    /* DEG_F32 | DEG_BF16 | DEG_FP8 (the copy must have been uploaded)  */
+    int32_t rerank;       /* precision != F32: keep this many candidates (>= k, <= 1024) and
+                             re-rank them on the float32 rows; 0 = k (no widening)           */
+    int32_t max_hops;     /* 0 = unlimited; else a query stops after this many expansions and
+                             reports DEG_EHOPLIMIT with its current result list               */
+    int32_t visited_cap;  /* on-chip visited-set slots per query (power of two), 0 = auto     */
+    int32_t queue_cap;    /* on-chip candidate slots per query, 0 = auto                      */
+} deg_search_params;
+
+/* Plain search: one Alg. 1 run per query q of queries_dev [nq][dim] float32, seeded at
+ * seeds_dev[q] (int32, nullable: NULL = the entry vertex of deg_upload). Seeds enter the result
+ * list (Alg. 1 line "R <- S"). Writes ids_dev [nq][k] int32 and dists_dev [nq][k] float32;
+ * status_dev (nullable) [nq] int32 gets DEG_OK or a per-query status. Exact: a query whose
+ * on-chip visited set or candidate queue would overflow is finished by a second kernel that
+ * keeps its state in device memory, with an identical result. */
+DEG_API deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
+                      const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
+                      int32_t* status_dev, void* stream);
+
+/* Exploration (Sec. 5.7): query q is the indexed vertex vertex_ids_dev[q]; the search starts
+ * at that vertex and never returns it (the user has already seen it). */
+DEG_API deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, int64_t nq, int32_t k,
+                       float eps, int32_t* ids_dev, float* dists_dev, int32_t* status_dev,
+                       void* stream);
+
+/* Full form of both. queries_dev is NULL iff explore != 0 (then seeds_dev holds the vertex
+ * ids). trace_dev (nullable) [nq][4] int32 receives per query: hops H (expansions), vertices
+ * evaluated E (= |C|), the candidate-queue high-water mark, and 1 if the query was finished by
+ * the device-memory kernel. */
+DEG_API deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, const float* queries_dev,
+                         const int32_t* seeds_dev, int32_t explore, int64_t nq, int32_t* ids_dev,
+                         float* dists_dev, int32_t* status_dev, int32_t* trace_dev, void* stream);
+
+/* End-to-end form with HOST buffers: copies queries_host [nq][dim] (or the vertex ids in
+ * seeds_host when explore != 0) to the device, searches, copies ids/dists back into
+ * ids_host [nq][k] / dists_host [nq][k], and synchronises `stream` before returning. Uses
+ * device buffers cached in the index (grown on demand). */
+DEG_API deg_status deg_search_host(deg_index* idx, const deg_search_params* p, const float* queries_host,
+                           const int32_t* seeds_host, int32_t explore, int64_t nq,
+                           int32_t* ids_host, float* dists_host, void* stream);
+
+/* ---- exact ground truth (Eq. 1) ----------------------------------------------------------- */
+
+/* Exact k nearest neighbours of queries_dev [nq][dim] among base_dev [n][dim] (float32 rows,
+ * row-major, dim floats apart), 1 <= k <= 256. Distances are the float32 Euclidean distances
+ * the library's search uses; ties go to the lower id. */
+DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
+                     int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
+
+/* Message of the last failed call on this thread ("" if none). */
+DEG_API const char* deg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEG_H */

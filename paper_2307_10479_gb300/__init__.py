@@ -1,6 +1,230 @@
 """GB300-native batched search over a Dynamic Exploration Graph (DEG, arXiv 2307.10479).
 
-The compute path lives in ``libdeg.so`` (hand-written CUDA for sm_103a behind a C ABI declared
-in ``include/deg.h``); this package is a thin ctypes binding with the same names. Importing the
-package does not load the library; the first call does, and raises if it is missing.
+The compute path lives in ``libdeg.so`` (hand-written CUDA for sm_103a behind the C ABI declared
+in ``include/deg.h``). This package is a thin ctypes binding with the same names: it marshals
+torch tensors and numpy arrays into pointers, sizes and the current CUDA stream, and raises on
+a non-zero status. Importing the package does not load the library; the first call does, and
+raises ``RuntimeError`` if the library has not been built (``__graft_entry__.build()``).
 """
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+DEG_OK, DEG_EINVAL, DEG_ENOMEM, DEG_ECUDA, DEG_EIO = 0, -1, -2, -3, -4
+DEG_EOVERFLOW, DEG_EHOPLIMIT, DEG_ETIMEOUT, DEG_EGRAPH, DEG_ENOTREADY = -5, -6, -7, -8, -9
+DEG_F32, DEG_BF16, DEG_FP8 = 0, 1, 2
+PRECISIONS = {"f32": DEG_F32, "bf16": DEG_BF16, "fp8": DEG_FP8}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DegError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"[deg status {status}] {msg}")
+        self.status = status
+
+
+class BuildParams(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int32), ("k_ext", ctypes.c_int32), ("eps_ext", ctypes.c_float),
+                ("k_opt", ctypes.c_int32), ("eps_opt", ctypes.c_float), ("i_opt", ctypes.c_int32),
+                ("refine_rounds", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class SearchParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("eps", ctypes.c_float), ("precision", ctypes.c_int32),
+                ("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("visited_cap", ctypes.c_int32),
+                ("queue_cap", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdeg.so (built in-tree). Raises RuntimeError if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libdeg.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        L = ctypes.CDLL(_build.LIB)
+        P, i32, i64, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        S = ctypes.c_int
+        sig = {
+            "deg_build": (S, [P, i64, i32, ctypes.POINTER(BuildParams), P, ctypes.POINTER(P)]),
+            "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
+            "deg_save": (S, [P, ctypes.c_char_p, i32]),
+            "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
+            "deg_index_info": (S, [P, ctypes.POINTER(i64), ctypes.POINTER(i32), ctypes.POINTER(i32)]),
+            "deg_get_adjacency": (S, [P, P]),
+            "deg_upload": (S, [P, i32, P]),
+            "deg_entry_vertex": (i32, [P]),
+            "deg_free": (None, [P]),
+            "deg_search": (S, [P, P, i64, i32, f32, P, P, P, P, P]),
+            "deg_explore": (S, [P, P, i64, i32, f32, P, P, P, P]),
+            "deg_search_ex": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P, P, P]),
+            "deg_search_host": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P]),
+            "knn_exact": (S, [P, i64, P, i64, i32, i32, P, P, P]),
+            "deg_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+        return _lib
+
+
+def _check(status: int):
+    if status != DEG_OK:
+        raise DegError(status, lib().deg_last_error().decode(errors="replace"))
+
+
+def _stream_ptr(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _require_cuda(t, dtype, name):
+    import torch
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return t
+
+
+class Index:
+    """A DEG over float32 vectors: host copy, optional device copy (after ``upload``)."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self._h = handle
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.deg_free(h)
+            self._h = None
+
+    # ---- construction ---------------------------------------------------------------------
+    @classmethod
+    def build(cls, base: np.ndarray, degree: int, k_ext: int, eps_ext: float, k_opt: int, eps_opt: float,
+              i_opt: int, refine_rounds: int = 0, seed: int = 0) -> "Index":
+        base = np.ascontiguousarray(base, np.float32)
+        p = BuildParams(degree, k_ext, eps_ext, k_opt, eps_opt, i_opt, refine_rounds, seed)
+        h = ctypes.c_void_p()
+        _check(lib().deg_build(base.ctypes.data, base.shape[0], base.shape[1], ctypes.byref(p), None, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def from_arrays(cls, base: np.ndarray, adj: np.ndarray) -> "Index":
+        base = np.ascontiguousarray(base, np.float32)
+        adj = np.ascontiguousarray(adj, np.int32)
+        h = ctypes.c_void_p()
+        _check(lib().deg_index_from_arrays(base.ctypes.data, adj.ctypes.data, base.shape[0], base.shape[1],
+                                           adj.shape[1], ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def load(cls, path: str, base: np.ndarray | None = None) -> "Index":
+        b = None if base is None else np.ascontiguousarray(base, np.float32)
+        h = ctypes.c_void_p()
+        _check(lib().deg_load(path.encode(), None if b is None else b.ctypes.data, ctypes.byref(h)))
+        return cls(h)
+
+    def save(self, path: str, with_vectors: bool = False):
+        _check(lib().deg_save(self._h, path.encode(), 1 if with_vectors else 0))
+
+    def info(self):
+        n, d, g = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().deg_index_info(self._h, ctypes.byref(n), ctypes.byref(d), ctypes.byref(g)))
+        return n.value, d.value, g.value
+
+    def adjacency(self) -> np.ndarray:
+        n, _, g = self.info()
+        out = np.empty((n, g), np.int32)
+        _check(lib().deg_get_adjacency(self._h, out.ctypes.data))
+        return out
+
+    # ---- device ---------------------------------------------------------------------------
+    def upload(self, precisions=("f32",), stream=None):
+        mask = 0
+        for p in precisions:
+            mask |= 1 << PRECISIONS[p]
+        _check(lib().deg_upload(self._h, mask, _stream_ptr(stream)))
+
+    @property
+    def entry_vertex(self) -> int:
+        return int(lib().deg_entry_vertex(self._h))
+
+    def search(self, queries=None, k: int = 10, eps: float = 0.1, seeds=None, explore: bool = False,
+               precision: str = "f32", rerank: int = 0, max_hops: int = 0, visited_cap: int = 0,
+               queue_cap: int = 0, with_status: bool = False, with_trace: bool = False, out=None, stream=None):
+        """Alg. 1 for a batch of queries (CUDA tensors). Returns (ids, dists[, status][, trace])."""
+        import torch
+        if explore:
+            seeds = _require_cuda(seeds, torch.int32, "vertex ids")
+            nq = seeds.shape[0]
+            dev = seeds.device
+        else:
+            queries = _require_cuda(queries, torch.float32, "queries")
+            seeds = _require_cuda(seeds, torch.int32, "seeds")
+            nq = queries.shape[0]
+            dev = queries.device
+        if out is None:
+            ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+            dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
+        else:
+            ids, dists = out
+        status = torch.empty(nq, dtype=torch.int32, device=dev) if with_status else None
+        trace = torch.empty((nq, 4), dtype=torch.int32, device=dev) if with_trace else None
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, max_hops, visited_cap, queue_cap)
+        _check(lib().deg_search_ex(self._h, ctypes.byref(p), None if explore else _dptr(queries), _dptr(seeds),
+                                   1 if explore else 0, nq, _dptr(ids), _dptr(dists), _dptr(status), _dptr(trace),
+                                   _stream_ptr(stream)))
+        res = [ids, dists]
+        if with_status:
+            res.append(status)
+        if with_trace:
+            res.append(trace)
+        return tuple(res)
+
+    def search_host(self, queries: np.ndarray | None, k: int, eps: float, explore_ids: np.ndarray | None = None,
+                    precision: str = "f32", rerank: int = 0, out=None, stream=None):
+        """End-to-end form: host arrays in and out (pinned numpy views recommended)."""
+        explore = explore_ids is not None
+        nq = explore_ids.shape[0] if explore else queries.shape[0]
+        ids, dists = out if out is not None else (np.empty((nq, k), np.int32), np.empty((nq, k), np.float32))
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0)
+        qptr = None if explore else ctypes.c_void_p(queries.ctypes.data)
+        sptr = ctypes.c_void_p(explore_ids.ctypes.data) if explore else None
+        _check(lib().deg_search_host(self._h, ctypes.byref(p), qptr, sptr, 1 if explore else 0, nq,
+                                     ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(dists.ctypes.data),
+                                     _stream_ptr(stream)))
+        return ids, dists
+
+
+def knn_exact(base, queries, k: int, stream=None):
+    """Eq. 1 on the device: exact k-NN of CUDA float32 queries among CUDA float32 base rows."""
+    import torch
+    base = _require_cuda(base, torch.float32, "base")
+    queries = _require_cuda(queries, torch.float32, "queries")
+    nq = queries.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    _check(lib().knn_exact(_dptr(base), base.shape[0], _dptr(queries), nq, base.shape[1], k, _dptr(ids),
+                           _dptr(dists), _stream_ptr(stream)))
+    return ids, dists

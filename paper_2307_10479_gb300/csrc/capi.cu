@@ -1,0 +1,410 @@
+// C ABI of libdeg: argument validation, index lifecycle, graph files and the host side of the
+// search and kNN calls. Every compute step runs in the library's CUDA kernels; this file only
+// checks, allocates, copies and launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "deg_internal.h"
+
+struct deg_index {
+    int64_t n = 0;
+    int32_t dim = 0;
+    int32_t degree = 0;
+    std::vector<float> x;        // [n][dim]
+    std::vector<int32_t> adj;    // [n][degree]
+    deg::DeviceIndex dev;
+    deg::Workspace ws;
+    int device = -1;
+    int32_t uploaded_mask = 0;
+};
+
+namespace deg {
+namespace {
+thread_local std::string g_last_error;
+
+constexpr char kMagic[8] = {'D', 'E', 'G', 'G', 'R', 'A', 'P', 'H'};
+constexpr uint32_t kVersion = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t flags;          // bit 0: vectors follow the adjacency
+    int64_t n;
+    int32_t dim;
+    int32_t degree;
+    uint64_t vec_checksum;   // FNV-1a 64 over the float32 bytes of the vectors
+    uint64_t reserved[3];
+};
+static_assert(sizeof(FileHeader) == 64, "header layout");
+
+uint64_t fnv1a(const void* p, size_t bytes) {
+    const uint8_t* b = static_cast<const uint8_t*>(p);
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < bytes; ++i) {
+        h ^= b[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+deg_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(DEG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// Graph invariants of Sec. 4.1 that the search relies on (entries in range, no loops, no
+// duplicates, symmetric, even degree >= 4). Connectivity is not required by the search.
+deg_status check_graph(const int32_t* adj, int64_t n, int32_t d) {
+    if (d < 4 || d % 2) return fail(DEG_EGRAPH, "degree must be even and >= 4");
+    for (int64_t u = 0; u < n; ++u) {
+        const int32_t* r = adj + u * d;
+        for (int32_t j = 0; j < d; ++j) {
+            const int32_t v = r[j];
+            if (v < 0 || v >= n) return fail(DEG_EGRAPH, "neighbour id out of range at vertex " + std::to_string(u));
+            if (v == u) return fail(DEG_EGRAPH, "self loop at vertex " + std::to_string(u));
+            for (int32_t i = 0; i < j; ++i)
+                if (r[i] == v) return fail(DEG_EGRAPH, "duplicate edge at vertex " + std::to_string(u));
+            const int32_t* b = adj + (int64_t)v * d;
+            bool back = false;
+            for (int32_t i = 0; i < d && !back; ++i) back = (b[i] == u);
+            if (!back) return fail(DEG_EGRAPH, "asymmetric edge " + std::to_string(u) + "-" + std::to_string(v));
+        }
+    }
+    return DEG_OK;
+}
+
+void free_device(deg_index* idx) {
+    DeviceIndex& d = idx->dev;
+    cudaFree(d.x32);
+    cudaFree(d.xbf);
+    cudaFree(d.x8);
+    cudaFree(d.scale8);
+    cudaFree(d.adj);
+    d = DeviceIndex{};
+    workspace_free(idx->ws);
+    idx->uploaded_mask = 0;
+}
+
+deg_index* new_index(int64_t n, int32_t dim, int32_t degree) {
+    deg_index* idx = new (std::nothrow) deg_index;
+    if (!idx) return nullptr;
+    try {
+        idx->n = n;
+        idx->dim = dim;
+        idx->degree = degree;
+        idx->x.resize((size_t)n * dim);
+        idx->adj.resize((size_t)n * degree);
+    } catch (const std::bad_alloc&) {
+        delete idx;
+        return nullptr;
+    }
+    return idx;
+}
+
+}  // namespace
+
+deg_status fail(deg_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+}  // namespace deg
+
+using namespace deg;
+
+extern "C" const char* deg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" deg_status deg_build(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
+                                volatile int64_t* progress, deg_index** out) {
+    if (!out) return fail(DEG_EINVAL, "deg_build: out is NULL");
+    *out = nullptr;
+    if (!base_host || !p) return fail(DEG_EINVAL, "deg_build: NULL argument");
+    if (dim <= 0) return fail(DEG_EINVAL, "deg_build: dim must be positive");
+    if (p->degree < 4 || p->degree % 2) return fail(DEG_EINVAL, "deg_build: degree must be even and >= 4");
+    if (p->degree > 256) return fail(DEG_EINVAL, "deg_build: degree must be <= 256");
+    if (n < p->degree + 1) return fail(DEG_EINVAL, "deg_build: need n >= degree + 1");
+    if (n > INT32_MAX) return fail(DEG_EINVAL, "deg_build: n must fit in int32");
+    if (p->k_ext < p->degree || p->k_opt < 1 || p->i_opt < 0 || p->refine_rounds < 0)
+        return fail(DEG_EINVAL, "deg_build: need k_ext >= degree, k_opt >= 1, i_opt >= 0");
+    if (!(p->eps_ext >= 0.f) || !(p->eps_opt >= 0.f)) return fail(DEG_EINVAL, "deg_build: eps must be >= 0");
+    deg_index* idx = new_index(n, dim, p->degree);
+    if (!idx) return fail(DEG_ENOMEM, "deg_build: host allocation failed");
+    std::memcpy(idx->x.data(), base_host, sizeof(float) * (size_t)n * dim);
+    try {
+        build_graph(idx->x.data(), n, dim, *p, idx->adj.data(), progress);
+    } catch (const std::exception& e) {
+        delete idx;
+        return fail(DEG_EGRAPH, std::string("deg_build: ") + e.what());
+    }
+    *out = idx;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_index_from_arrays(const float* base_host, const int32_t* adj_host, int64_t n,
+                                            int32_t dim, int32_t degree, deg_index** out) {
+    if (!out) return fail(DEG_EINVAL, "deg_index_from_arrays: out is NULL");
+    *out = nullptr;
+    if (!base_host || !adj_host || n <= 0 || dim <= 0) return fail(DEG_EINVAL, "deg_index_from_arrays: bad arguments");
+    if (n > INT32_MAX) return fail(DEG_EINVAL, "deg_index_from_arrays: n must fit in int32");
+    if (degree > 256) return fail(DEG_EINVAL, "deg_index_from_arrays: degree must be <= 256");
+    deg_status s = check_graph(adj_host, n, degree);
+    if (s != DEG_OK) return s;
+    deg_index* idx = new_index(n, dim, degree);
+    if (!idx) return fail(DEG_ENOMEM, "deg_index_from_arrays: host allocation failed");
+    std::memcpy(idx->x.data(), base_host, sizeof(float) * (size_t)n * dim);
+    std::memcpy(idx->adj.data(), adj_host, sizeof(int32_t) * (size_t)n * degree);
+    *out = idx;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_save(const deg_index* idx, const char* path, int32_t with_vectors) {
+    if (!idx || !path) return fail(DEG_EINVAL, "deg_save: NULL argument");
+    FileHeader h{};
+    std::memcpy(h.magic, kMagic, 8);
+    h.version = kVersion;
+    h.flags = with_vectors ? 1u : 0u;
+    h.n = idx->n;
+    h.dim = idx->dim;
+    h.degree = idx->degree;
+    h.vec_checksum = fnv1a(idx->x.data(), sizeof(float) * idx->x.size());
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(DEG_EIO, std::string("deg_save: cannot open ") + path);
+    bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 &&
+              std::fwrite(idx->adj.data(), sizeof(int32_t), idx->adj.size(), f) == idx->adj.size();
+    if (ok && with_vectors) ok = std::fwrite(idx->x.data(), sizeof(float), idx->x.size(), f) == idx->x.size();
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? DEG_OK : fail(DEG_EIO, std::string("deg_save: write failed for ") + path);
+}
+
+extern "C" deg_status deg_load(const char* path, const float* base_host, deg_index** out) {
+    if (!out || !path) return fail(DEG_EINVAL, "deg_load: NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(DEG_EIO, std::string("deg_load: cannot open ") + path);
+    FileHeader h{};
+    if (std::fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, kMagic, 8) || h.version != kVersion ||
+        h.n <= 0 || h.n > INT32_MAX || h.dim <= 0 || h.degree < 4 || h.degree > 256) {
+        std::fclose(f);
+        return fail(DEG_EIO, std::string("deg_load: bad header in ") + path);
+    }
+    const bool has_vec = h.flags & 1u;
+    if (!has_vec && !base_host) {
+        std::fclose(f);
+        return fail(DEG_EINVAL, "deg_load: file has no vectors and base_host is NULL");
+    }
+    deg_index* idx = new_index(h.n, h.dim, h.degree);
+    if (!idx) {
+        std::fclose(f);
+        return fail(DEG_ENOMEM, "deg_load: host allocation failed");
+    }
+    bool ok = std::fread(idx->adj.data(), sizeof(int32_t), idx->adj.size(), f) == idx->adj.size();
+    if (ok && has_vec) ok = std::fread(idx->x.data(), sizeof(float), idx->x.size(), f) == idx->x.size();
+    std::fclose(f);
+    if (!ok) {
+        delete idx;
+        return fail(DEG_EIO, std::string("deg_load: truncated file ") + path);
+    }
+    if (!has_vec) {
+        std::memcpy(idx->x.data(), base_host, sizeof(float) * idx->x.size());
+        if (fnv1a(idx->x.data(), sizeof(float) * idx->x.size()) != h.vec_checksum) {
+            delete idx;
+            return fail(DEG_EIO, "deg_load: base_host does not match the vectors the graph was built on");
+        }
+    }
+    deg_status s = check_graph(idx->adj.data(), idx->n, idx->degree);
+    if (s != DEG_OK) {
+        delete idx;
+        return s;
+    }
+    *out = idx;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_index_info(const deg_index* idx, int64_t* n, int32_t* dim, int32_t* degree) {
+    if (!idx) return fail(DEG_EINVAL, "deg_index_info: NULL index");
+    if (n) *n = idx->n;
+    if (dim) *dim = idx->dim;
+    if (degree) *degree = idx->degree;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_get_adjacency(const deg_index* idx, int32_t* adj_host) {
+    if (!idx || !adj_host) return fail(DEG_EINVAL, "deg_get_adjacency: NULL argument");
+    std::memcpy(adj_host, idx->adj.data(), sizeof(int32_t) * idx->adj.size());
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* stream) {
+    if (!idx) return fail(DEG_EINVAL, "deg_upload: NULL index");
+    if (precision_mask & ~((1 << DEG_BF16) | (1 << DEG_FP8) | (1 << DEG_F32)))
+        return fail(DEG_EINVAL, "deg_upload: unknown precision bit");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "deg_upload: cudaGetDevice");
+    if (idx->dev.x32 && idx->device != dev) free_device(idx);
+    DeviceIndex& d = idx->dev;
+    std::string why;
+    if (!d.x32) {
+        d.n = idx->n;
+        d.dim = idx->dim;
+        d.dim_pad = (idx->dim + 3) / 4 * 4;
+        d.degree = idx->degree;
+        d.deg_pad = (idx->degree + 3) / 4 * 4;
+        const size_t xb = sizeof(float) * (size_t)d.n * d.dim_pad;
+        const size_t ab = sizeof(int32_t) * (size_t)d.n * d.deg_pad;
+        if ((e = cudaMalloc(&d.x32, xb)) != cudaSuccess || (e = cudaMalloc(&d.adj, ab)) != cudaSuccess) {
+            free_device(idx);
+            return fail(DEG_ENOMEM, std::string("deg_upload: cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        // Strided 2-D copies place each row at its padded stride; padding is zero / -1.
+        if ((e = cudaMemsetAsync(d.x32, 0, xb, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(d.x32, sizeof(float) * d.dim_pad, idx->x.data(), sizeof(float) * d.dim,
+                                   sizeof(float) * d.dim, d.n, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(d.adj, 0xff, ab, st)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(d.adj, sizeof(int32_t) * d.deg_pad, idx->adj.data(), sizeof(int32_t) * d.degree,
+                                   sizeof(int32_t) * d.degree, d.n, cudaMemcpyHostToDevice, st)) != cudaSuccess) {
+            free_device(idx);
+            return cuda_fail(e, "deg_upload: copy");
+        }
+        idx->device = dev;
+        idx->uploaded_mask = 1 << DEG_F32;
+        if (compute_entry_vertex(d, st, &why) != 0) {
+            free_device(idx);
+            return fail(DEG_ECUDA, "deg_upload: entry vertex: " + why);
+        }
+    }
+    if ((precision_mask & (1 << DEG_BF16)) && !d.xbf) {
+        if (make_bf16_copy(d, st, &why) != 0) return fail(DEG_ECUDA, "deg_upload: bf16 copy: " + why);
+        idx->uploaded_mask |= 1 << DEG_BF16;
+    }
+    if ((precision_mask & (1 << DEG_FP8)) && !d.x8) {
+        if (make_fp8_copy(d, st, &why) != 0) return fail(DEG_ECUDA, "deg_upload: fp8 copy: " + why);
+        idx->uploaded_mask |= 1 << DEG_FP8;
+    }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "deg_upload: synchronize");
+    return DEG_OK;
+}
+
+extern "C" int32_t deg_entry_vertex(const deg_index* idx) { return idx ? idx->dev.entry : -1; }
+
+extern "C" void deg_free(deg_index* idx) {
+    if (!idx) return;
+    free_device(idx);
+    delete idx;
+}
+
+namespace {
+
+deg_status validate_search(const deg_index* idx, const deg_search_params* p, const float* queries,
+                           const int32_t* seeds, int32_t explore, int64_t nq) {
+    if (!idx || !p) return fail(DEG_EINVAL, "search: NULL index or params");
+    if (!idx->dev.x32) return fail(DEG_ENOTREADY, "search: index not uploaded (call deg_upload)");
+    if (nq < 0 || nq > INT32_MAX) return fail(DEG_EINVAL, "search: nq out of range");
+    if (p->k < 1 || p->k > 1024) return fail(DEG_EINVAL, "search: k must be in [1, 1024]");
+    if (explore ? p->k > idx->n - 1 : p->k > idx->n) return fail(DEG_EINVAL, "search: k larger than the candidates");
+    if (!(p->eps >= 0.f) || std::isinf(p->eps)) return fail(DEG_EINVAL, "search: eps must be finite and >= 0");
+    if (p->precision < DEG_F32 || p->precision > DEG_FP8) return fail(DEG_EINVAL, "search: unknown precision");
+    if (!(idx->uploaded_mask & (1 << p->precision))) return fail(DEG_ENOTREADY, "search: precision copy not uploaded");
+    if (p->rerank < 0 || p->rerank > 1024 || (p->rerank && p->rerank < p->k))
+        return fail(DEG_EINVAL, "search: rerank must be 0 or in [k, 1024]");
+    if (p->max_hops < 0) return fail(DEG_EINVAL, "search: max_hops must be >= 0");
+    if (p->visited_cap < 0 || (p->visited_cap & (p->visited_cap - 1)) || p->visited_cap > (1 << 16))
+        return fail(DEG_EINVAL, "search: visited_cap must be 0 or a power of two <= 65536");
+    if (p->queue_cap < 0 || p->queue_cap > (1 << 14)) return fail(DEG_EINVAL, "search: queue_cap out of range");
+    if (explore ? (queries != nullptr || seeds == nullptr) : (queries == nullptr && nq > 0))
+        return fail(DEG_EINVAL, "search: explore needs vertex ids and no query vectors; search needs vectors");
+    return DEG_OK;
+}
+
+}  // namespace
+
+extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, const float* queries_dev,
+                                    const int32_t* seeds_dev, int32_t explore, int64_t nq, int32_t* ids_dev,
+                                    float* dists_dev, int32_t* status_dev, int32_t* trace_dev, void* stream) {
+    deg_status s = validate_search(idx, p, queries_dev, seeds_dev, explore, nq);
+    if (s != DEG_OK) return s;
+    if (nq == 0) return DEG_OK;
+    if (!ids_dev || !dists_dev) return fail(DEG_EINVAL, "search: NULL output");
+    std::string why;
+    if (workspace_reserve(idx->ws, idx->dev, nq, &why) != 0) return fail(DEG_ENOMEM, "search: workspace: " + why);
+    SearchArgs a{&idx->dev, queries_dev, seeds_dev, explore ? 1 : 0, nq, p->k, p->eps, p->precision,
+                 p->rerank, p->max_hops, p->visited_cap, p->queue_cap, ids_dev, dists_dev, status_dev, trace_dev};
+    const int e = launch_search(a, idx->ws, static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "search: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
+                                 const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
+                                 int32_t* status_dev, void* stream) {
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0};
+    return deg_search_ex(idx, &p, queries_dev, seeds_dev, 0, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
+}
+
+extern "C" deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, int64_t nq, int32_t k,
+                                  float eps, int32_t* ids_dev, float* dists_dev, int32_t* status_dev,
+                                  void* stream) {
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0};
+    return deg_search_ex(idx, &p, nullptr, vertex_ids_dev, 1, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
+}
+
+extern "C" deg_status deg_search_host(deg_index* idx, const deg_search_params* p, const float* queries_host,
+                                      const int32_t* seeds_host, int32_t explore, int64_t nq, int32_t* ids_host,
+                                      float* dists_host, void* stream) {
+    deg_status s = validate_search(idx, p, queries_host, seeds_host, explore, nq);
+    if (s != DEG_OK) return s;
+    if (nq == 0) return DEG_OK;
+    if (!ids_host || !dists_host) return fail(DEG_EINVAL, "search_host: NULL output");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Workspace& ws = idx->ws;
+    cudaError_t e;
+    const int64_t row = explore ? 0 : idx->dim;
+    if (ws.stage_q < nq || ws.stage_k < p->k) {
+        cudaFree(ws.dq);
+        cudaFree(ws.did);
+        cudaFree(ws.dd);
+        ws.dq = ws.did = ws.dd = nullptr;
+        ws.stage_q = ws.stage_k = 0;
+        const size_t qb = std::max<size_t>(sizeof(float) * (size_t)nq * idx->dim, sizeof(int32_t) * (size_t)nq);
+        if ((e = cudaMalloc(&ws.dq, qb)) != cudaSuccess || (e = cudaMalloc(&ws.did, sizeof(int32_t) * nq * p->k)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.dd, sizeof(float) * nq * p->k)) != cudaSuccess)
+            return fail(DEG_ENOMEM, std::string("search_host: cudaMalloc: ") + cudaGetErrorString(e));
+        ws.stage_q = nq;
+        ws.stage_k = p->k;
+    }
+    if (!explore && seeds_host) return fail(DEG_EINVAL, "search_host: per-query seeds are not supported with host buffers");
+    const size_t in_bytes = explore ? sizeof(int32_t) * nq : sizeof(float) * nq * row;
+    if ((e = cudaMemcpyAsync(ws.dq, explore ? (const void*)seeds_host : (const void*)queries_host, in_bytes,
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(e, "search_host: H2D");
+    const float* q = explore ? nullptr : static_cast<const float*>(ws.dq);
+    const int32_t* sd = explore ? static_cast<const int32_t*>(ws.dq) : nullptr;
+    s = deg_search_ex(idx, p, q, sd, explore, nq, static_cast<int32_t*>(ws.did), static_cast<float*>(ws.dd),
+                      nullptr, nullptr, stream);
+    if (s != DEG_OK) return s;
+    if ((e = cudaMemcpyAsync(ids_host, ws.did, sizeof(int32_t) * nq * p->k, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(dists_host, ws.dd, sizeof(float) * nq * p->k, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(e, "search_host: D2H");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "search_host: synchronize");
+    return DEG_OK;
+}
+
+extern "C" deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
+                                int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream) {
+    if (n <= 0 || n > INT32_MAX || nq < 0 || nq > INT32_MAX || dim <= 0) return fail(DEG_EINVAL, "knn_exact: bad sizes");
+    if (k < 1 || k > 256) return fail(DEG_EINVAL, "knn_exact: k must be in [1, 256]");
+    if (k > n) return fail(DEG_EINVAL, "knn_exact: k larger than n");
+    if (nq == 0) return DEG_OK;
+    if (!base_dev || !queries_dev || !ids_dev || !dists_dev) return fail(DEG_EINVAL, "knn_exact: NULL argument");
+    std::string why;
+    const int e = launch_knn_exact(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
+                                   static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) return fail(DEG_ECUDA, "knn_exact: " + why);
+    return DEG_OK;
+}

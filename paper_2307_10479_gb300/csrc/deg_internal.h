@@ -1,0 +1,95 @@
+// Internal declarations of libdeg (not part of the C ABI).
+#ifndef DEG_INTERNAL_H
+#define DEG_INTERNAL_H
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/deg.h"
+
+struct CUstream_st;
+typedef CUstream_st* deg_stream_t;
+
+namespace deg {
+
+// Host-side graph construction (builder.cpp).
+int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& p, int32_t* adj_out,
+                volatile int64_t* progress);
+
+// Record an error message for deg_last_error() and return the status.
+deg_status fail(deg_status s, const std::string& msg);
+
+// Device copy of an index (everything the kernels read), owned by deg_index.
+struct DeviceIndex {
+    int64_t n = 0;
+    int32_t dim = 0;          // logical dimension
+    int32_t dim_pad = 0;      // float32 row stride in elements (multiple of 4)
+    int32_t degree = 0;       // logical degree
+    int32_t deg_pad = 0;      // adjacency row stride in int32 (multiple of 4)
+    float* x32 = nullptr;     // [n][dim_pad] float32, zero padded
+    uint16_t* xbf = nullptr;  // [n][dim_pad16] bfloat16 (optional)
+    int32_t dim_pad16 = 0;    // bf16 row stride (multiple of 8)
+    uint8_t* x8 = nullptr;    // [n][dim_pad8] E4M3 codes (optional)
+    float* scale8 = nullptr;  // [n] per-row scale of the E4M3 codes
+    int32_t dim_pad8 = 0;     // fp8 row stride (multiple of 16)
+    int32_t* adj = nullptr;   // [n][deg_pad], padded slots = -1
+    int32_t entry = -1;
+};
+
+// Scratch for one search call: the overflow list, and the per-slot device-memory state of the
+// second (device-memory) kernel.
+struct Workspace {
+    int32_t* counters = nullptr;     // [0] overflow count, [1] work cursor of the 2nd kernel
+    int32_t* overflow = nullptr;     // [cap_q] query indices
+    int64_t cap_q = 0;
+    uint32_t* bitmaps = nullptr;     // [slots][words] visited bitmaps
+    uint64_t* pools = nullptr;       // [slots][n + 1] candidate keys
+    uint64_t* results = nullptr;     // [slots][1024] result keys
+    int32_t slots = 0;
+    int64_t words = 0;
+    // host e2e staging
+    void* dq = nullptr;
+    void* did = nullptr;
+    void* dd = nullptr;
+    int64_t stage_q = 0, stage_k = 0;
+};
+
+struct SearchArgs {
+    const DeviceIndex* ix;
+    const float* queries;     // [nq][dim] (row stride dim) or nullptr when explore
+    const int32_t* seeds;     // [nq] or nullptr (entry vertex)
+    int32_t explore;
+    int64_t nq;
+    int32_t k;
+    float eps;
+    int32_t precision;
+    int32_t rerank;
+    int32_t max_hops;
+    int32_t visited_cap;
+    int32_t queue_cap;
+    int32_t* ids;
+    float* dists;
+    int32_t* status;
+    int32_t* trace;
+};
+
+// Kernel launchers (search.cu). Return a cudaError_t value (0 = success).
+int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::string* why);
+int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::string* why);
+void workspace_free(Workspace& ws);
+
+// Entry vertex (entry.cu): lower median per coordinate, then the nearest row. Synchronous.
+int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+
+// Reduced-precision copies (quantize.cu).
+int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+int make_fp8_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+
+// Exact kNN (knn_exact.cu).
+int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
+                     int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
+
+}  // namespace deg
+
+#endif

@@ -105,6 +105,11 @@ DEG_API deg_status deg_get_adjacency(const deg_index* idx, int32_t* adj_host);
  * -- the paper's "median vertex" (Sec. 4.4). Synchronises `stream` before returning. */
 DEG_API deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* stream);
 
+/* Copy the device's reduced-precision rows out to the host, unpadded: precision DEG_BF16 ->
+ * codes_host [n][dim] uint16 (bfloat16 bit patterns); DEG_FP8 -> codes_host [n][dim] uint8
+ * (E4M3 codes) and scales_host [n] float32. DEG_ENOTREADY if that copy was not uploaded. */
+DEG_API deg_status deg_export_codes(const deg_index* idx, int32_t precision, void* codes_host, float* scales_host);
+
 /* The entry vertex computed by deg_upload, or -1 before it. */
 DEG_API int32_t deg_entry_vertex(const deg_index* idx);
 

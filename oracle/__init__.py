@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["oracle_search.cpp", "oracle_build.cpp"]
+_SRCS = ["oracle_search.cpp", "oracle_build.cpp", "oracle_quant.cpp"]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -60,6 +60,11 @@ def lib() -> ctypes.CDLL:
             L.oracle_check_mrng.restype = i32
             L.oracle_optimize_edge.argtypes = [P, i64, i32, P, i32, i32, i32, i32, i32, f64]
             L.oracle_optimize_edge.restype = i32
+            L.oracle_quantize_bf16.argtypes = [P, i64, i32, P]
+            L.oracle_quantize_fp8.argtypes = [P, i64, i32, P, P]
+            L.oracle_decode.argtypes = [i32, P, P, i64, i32, P]
+            L.oracle_range_search_decoded.argtypes = [P, P, i64, i32, P, i32, P, P, i64, i32, i32, i32, f64, P, P, i32]
+            L.oracle_range_search_decoded.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -164,3 +169,47 @@ def optimize_edge(base, adj, v1, v2, i_opt, k_opt, eps_opt):
     if rc < 0:
         raise ValueError(f"oracle_optimize_edge failed ({rc})")
     return rc == 1, out
+
+
+def quantize_bf16(x):
+    """bfloat16 bit patterns (uint16) of float32 x, round to nearest even."""
+    x = _f32(x)
+    out = np.empty(x.shape, np.uint16)
+    lib().oracle_quantize_bf16(_ptr(x), x.shape[0], x.shape[1], _ptr(out))
+    return out
+
+
+def quantize_fp8(x):
+    """Per-row scaled FP8 E4M3 codes (uint8) and float32 scales of float32 x."""
+    x = _f32(x)
+    codes = np.empty(x.shape, np.uint8)
+    scales = np.empty(x.shape[0], np.float32)
+    lib().oracle_quantize_fp8(_ptr(x), x.shape[0], x.shape[1], _ptr(codes), _ptr(scales))
+    return codes, scales
+
+
+def decode(precision, codes, scales=None):
+    """Exact FP64 values of bf16 (precision 'bf16') or scaled fp8 ('fp8') codes."""
+    codes = np.ascontiguousarray(codes)
+    sc = None if scales is None else np.ascontiguousarray(scales, np.float32)
+    out = np.empty(codes.shape, np.float64)
+    lib().oracle_decode(1 if precision == "bf16" else 2, _ptr(codes), _ptr(sc), codes.shape[0], codes.shape[1], _ptr(out))
+    return out
+
+
+def range_search_decoded(decoded, base, adj, queries, seeds, k, eps, keep=None, explore=False, nthreads=None):
+    """Alg. 1 on decoded reduced-precision rows keeping `keep` (>= k) results, re-ranked on the
+    float32 rows -> (ids, dists)."""
+    decoded = np.ascontiguousarray(decoded, np.float64)
+    base, adj, seeds = _f32(base), _i32(adj), _i32(seeds)
+    nq = seeds.shape[0]
+    q = None if explore else _f32(queries)
+    ids = np.empty((nq, k), np.int32)
+    dists = np.empty((nq, k), np.float64)
+    rc = lib().oracle_range_search_decoded(_ptr(decoded), _ptr(base), base.shape[0], base.shape[1], _ptr(adj),
+                                           adj.shape[1], _ptr(q), _ptr(seeds), nq, 1 if explore else 0,
+                                           keep or k, k, float(eps), _ptr(ids), _ptr(dists),
+                                           nthreads or default_threads())
+    if rc:
+        raise ValueError("oracle_range_search_decoded: invalid arguments")
+    return ids, dists

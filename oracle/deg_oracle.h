@@ -70,6 +70,18 @@ int32_t oracle_optimize_edge(const float* base, int64_t n, int32_t dim, int32_t*
                              int32_t degree, int32_t v1, int32_t v2, int32_t i_opt,
                              int32_t k_opt, double eps_opt);
 
+/* Reduced-precision stores (format definitions: bfloat16 RNE; FP8 E4M3 with a per-row scale
+ * s = max|x|/448, codes RNE and saturated) and the search over them with an FP64 re-rank. */
+int oracle_quantize_bf16(const float* x, int64_t n, int32_t dim, uint16_t* out);
+int oracle_quantize_fp8(const float* x, int64_t n, int32_t dim, uint8_t* codes, float* scales);
+/* precision 1 = bf16 codes (uint16), 2 = fp8 codes (uint8) with scales -> FP64 values [n][dim]. */
+int oracle_decode(int32_t precision, const void* codes, const float* scales, int64_t n, int32_t dim, double* out);
+/* Alg. 1 over the decoded rows keeping `keep` results, then re-rank on the float32 rows. */
+int oracle_range_search_decoded(const double* dec, const float* base, int64_t n, int32_t dim,
+                                const int32_t* adj, int32_t degree, const float* queries,
+                                const int32_t* seeds, int64_t nq, int32_t explore, int32_t keep,
+                                int32_t k, double eps, int32_t* ids, double* dists, int32_t nthreads);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
             "deg_get_adjacency": (S, [P, P]),
             "deg_upload": (S, [P, i32, P]),
             "deg_entry_vertex": (i32, [P]),
+            "deg_export_codes": (S, [P, i32, P, P]),
             "deg_free": (None, [P]),
             "deg_search": (S, [P, P, i64, i32, f32, P, P, P, P, P]),
             "deg_explore": (S, [P, P, i64, i32, f32, P, P, P, P]),
@@ -165,6 +166,18 @@ class Index:
         for p in precisions:
             mask |= 1 << PRECISIONS[p]
         _check(lib().deg_upload(self._h, mask, _stream_ptr(stream)))
+
+    def export_codes(self, precision: str):
+        """The device's reduced-precision rows: bf16 -> uint16 [n, dim]; fp8 -> (uint8 [n, dim], scales)."""
+        n, dim, _ = self.info()
+        if precision == "bf16":
+            codes = np.empty((n, dim), np.uint16)
+            _check(lib().deg_export_codes(self._h, DEG_BF16, codes.ctypes.data, None))
+            return codes
+        codes = np.empty((n, dim), np.uint8)
+        scales = np.empty(n, np.float32)
+        _check(lib().deg_export_codes(self._h, DEG_FP8, codes.ctypes.data, scales.ctypes.data))
+        return codes, scales
 
     @property
     def entry_vertex(self) -> int:

@@ -293,6 +293,25 @@ extern "C" deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* s
 
 extern "C" int32_t deg_entry_vertex(const deg_index* idx) { return idx ? idx->dev.entry : -1; }
 
+extern "C" deg_status deg_export_codes(const deg_index* idx, int32_t precision, void* codes_host, float* scales_host) {
+    if (!idx || !codes_host) return fail(DEG_EINVAL, "deg_export_codes: NULL argument");
+    const DeviceIndex& d = idx->dev;
+    cudaError_t e;
+    if (precision == DEG_BF16) {
+        if (!d.xbf) return fail(DEG_ENOTREADY, "deg_export_codes: bf16 copy not uploaded");
+        e = cudaMemcpy2D(codes_host, 2 * (size_t)d.dim, d.xbf, 2 * (size_t)d.dim_pad16, 2 * (size_t)d.dim, d.n,
+                         cudaMemcpyDeviceToHost);
+    } else if (precision == DEG_FP8) {
+        if (!d.x8) return fail(DEG_ENOTREADY, "deg_export_codes: fp8 copy not uploaded");
+        if (!scales_host) return fail(DEG_EINVAL, "deg_export_codes: scales_host is NULL");
+        e = cudaMemcpy2D(codes_host, (size_t)d.dim, d.x8, (size_t)d.dim_pad8, (size_t)d.dim, d.n, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(scales_host, d.scale8, sizeof(float) * d.n, cudaMemcpyDeviceToHost);
+    } else {
+        return fail(DEG_EINVAL, "deg_export_codes: precision must be DEG_BF16 or DEG_FP8");
+    }
+    return e == cudaSuccess ? DEG_OK : cuda_fail(e, "deg_export_codes");
+}
+
 extern "C" void deg_free(deg_index* idx) {
     if (!idx) return;
     free_device(idx);

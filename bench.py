@@ -34,7 +34,7 @@ TARGET_RECALL = 0.95
 EPS_GRID = [round(0.02 * i, 2) for i in range(0, 21)]
 METRIC = "QPS at recall@10>=0.95 (1M x 128), vs plain FP32 search; p50/p99 ms; HBM GB/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
-TRAFFIC = os.path.join(ROOT, "profiles", "search_traffic.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "search_traffic.txt")
 
 
 def log(*a):
@@ -63,12 +63,16 @@ def source_digest():
 
 
 def recorded_traffic():
-    """DRAM bytes per launch of the search kernel from the last ncu capture, if the kernel source
-    is unchanged since (else null)."""
+    """DRAM bytes per launch of the search kernel from the last ncu capture (profiles/), if the
+    kernel source is unchanged since (else null)."""
     try:
-        t = json.load(open(TRAFFIC))
-        if t.get("source_digest") == source_digest() and t.get("workload") == WORKLOAD:
-            return t["dram_bytes_per_launch"]
+        kv = {}
+        for line in open(TRAFFIC):
+            if ":" in line and not line.startswith("#"):
+                key, val = line.split(":", 1)
+                kv[key.strip()] = val.strip()
+        if kv.get("source_digest") == source_digest() and kv.get("workload") == WORKLOAD:
+            return int(kv["dram_bytes_per_launch"])
     except Exception:
         pass
     return None
@@ -266,6 +270,7 @@ def main():
     qd = torch.from_numpy(q).cuda()
     gt_ids, _ = deg.knn_exact(torch.from_numpy(base).cuda(), qd, K)
     gt = gt_ids.cpu().numpy()
+    torch.cuda.empty_cache()
     if args.eps is None:
         eps, rec = pick_eps(idx, qd, gt)
     else:

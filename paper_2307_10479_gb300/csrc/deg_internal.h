@@ -43,11 +43,14 @@ struct Workspace {
     int32_t* counters = nullptr;     // [0] overflow count, [1] work cursor of the 2nd kernel
     int32_t* overflow = nullptr;     // [cap_q] query indices
     int64_t cap_q = 0;
-    uint32_t* bitmaps = nullptr;     // [slots][words] visited bitmaps
-    uint64_t* pools = nullptr;       // [slots][n + 1] candidate keys
-    uint64_t* results = nullptr;     // [slots][1024] result keys
+    int64_t words = 0;               // 32-bit words of one visited bitmap
+    uint32_t* ibitmaps = nullptr;    // device mode of the fast kernel: [islots][words]
+    uint64_t* ipools = nullptr;      //   [islots][ipcap] candidate keys
+    int32_t islots = 0, ipcap = 0;
+    uint32_t* bitmaps = nullptr;     // second kernel: [slots][words] visited bitmaps
+    uint64_t* pools = nullptr;       //   [slots][n + 1] candidate keys
+    uint64_t* results = nullptr;     //   [slots][1024] result keys
     int32_t slots = 0;
-    int64_t words = 0;
     // host e2e staging
     void* dq = nullptr;
     void* did = nullptr;

@@ -139,7 +139,8 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     if (k > n) return *why = "k larger than n", (int)cudaErrorInvalidValue;
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(2ll << 30) / (4 * n)));
     float* D = nullptr;
-    cudaError_t e = cudaMallocAsync(&D, sizeof(float) * chunk * n, st);
+    // A plain allocation, released before returning (the call is a one-off: ground truth).
+    cudaError_t e = cudaMalloc(&D, sizeof(float) * chunk * n);
     if (e != cudaSuccess) return *why = std::string("distance buffer: ") + cudaGetErrorString(e), (int)e;
     for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
         const int64_t qc = std::min(chunk, nq - q0);
@@ -148,7 +149,8 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
         select_topk_kernel<<<(unsigned)qc, kSelThreads, 0, st>>>(D, n, k, ids + q0 * k, dists + q0 * k);
         if ((e = cudaGetLastError()) != cudaSuccess) break;
     }
-    cudaFreeAsync(D, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(D);
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;
 }

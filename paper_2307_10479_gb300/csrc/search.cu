@@ -19,11 +19,13 @@
 // queries search from their own vertex but never return it; r = +inf until R first exceeds k;
 // (distance, id) orders S and R, the lower id first.
 //
-// Two tiers. The fast kernel keeps C as an open-addressing hash table, S as an unsorted pool
-// and R as an unsorted array with a tracked maximum, all in shared memory. A query that would
-// overflow the hash table (load above 3/4) or the pool is abandoned and recorded in an overflow
-// list; a second kernel then reruns it from the start with C as an n-bit bitmap, S with room
-// for n candidates and R in device memory, so every query is answered exactly.
+// Three tiers, one result. The fast path keeps C as an open-addressing hash table, S as an
+// unsorted pool (argmin by a warp reduction) and R as a sorted array, all in shared memory.
+// A query that would overflow the hash table (load above 3/4) or the pool is rerun at once by
+// the same warp in device-memory mode: C becomes an n-bit bitmap and S a larger pool in the
+// warp's own slot of device memory. A query that overflows even that is recorded in an
+// overflow list and finished by a second kernel whose pool has room for all n vertices.
+// Every tier runs the same code on the same data, so the result does not depend on the tier.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -41,6 +43,7 @@ constexpr uint64_t kEmptyKey = ~0ull;
 constexpr uint32_t kEmptySlot = 0xffffffffu;
 constexpr int kMaxDegree = 128;
 constexpr int kMaxK = 1024;
+constexpr int kInlinePool = 32768;   // candidate pool of the device mode inside the fast kernel
 
 __device__ __forceinline__ uint64_t make_key(float d2, int32_t id) {
     return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)id;
@@ -56,11 +59,6 @@ __device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
 __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 #pragma unroll
     for (int m = 16; m; m >>= 1) v = min(v, shfl_xor64(v, m));
-    return v;
-}
-__device__ __forceinline__ uint64_t warp_max64(uint64_t v) {
-#pragma unroll
-    for (int m = 16; m; m >>= 1) v = max(v, shfl_xor64(v, m));
     return v;
 }
 
@@ -154,10 +152,13 @@ struct Params {
     // workspace
     int32_t* counters;         // [0] overflow count, [1] 2nd-kernel cursor, [2] fast cursor
     int32_t* overflow;
-    uint32_t* bitmaps;
-    uint64_t* pools;
-    uint64_t* results;
-    int64_t words;
+    int64_t words;             // 32-bit words of one visited bitmap (multiple of 4)
+    uint32_t* ibitmaps;        // device mode inside the fast kernel: [islots][words]
+    uint64_t* ipools;          //   [islots][ipcap]
+    int32_t islots, ipcap;
+    uint32_t* bitmaps;         // second kernel: [slots][words]
+    uint64_t* pools;           //   [slots][n + 1]
+    uint64_t* results;         //   [slots][kMaxK]
 };
 
 // Per-warp search state. All scalar members are warp-uniform (every lane holds the same value).
@@ -172,8 +173,6 @@ struct WarpState {
     int32_t pool_n, res_n;
     bool trimmed;
     float r2;
-    uint64_t maxkey;
-    int32_t maxpos;
     int32_t hops, evals, pool_hw;
 };
 
@@ -271,34 +270,33 @@ __device__ __forceinline__ int visit_bitmap(uint32_t* bm, int32_t id) {
     return (old & bit) ? 0 : 1;
 }
 
-// Insert key c into R (sequential semantics of Alg. 1 lines "R <- R u {n}; trim to k").
+// Insert key c into R, kept sorted ascending in res[0..res_n) (Alg. 1: R <- R u {n}; if |R| > k,
+// drop argmax and set r = max R). r stays +inf until R first overflows k.
 __device__ __forceinline__ void result_insert(WarpState& W, int ks, uint64_t c, int lane) {
-    if (W.res_n < ks) {
-        if (lane == 0) W.res[W.res_n] = c;
-        if (c > W.maxkey || W.res_n == 0) {
-            W.maxkey = c;
-            W.maxpos = W.res_n;
-        }
-        ++W.res_n;
-        __syncwarp();
-        return;
+    int pos = 0;
+    for (int i0 = 0; i0 < W.res_n; i0 += 32) {
+        const int i = i0 + lane;
+        pos += __popc(__ballot_sync(0xffffffffu, i < W.res_n && W.res[i] < c));
     }
-    W.trimmed = true;
-    if (c < W.maxkey) {
-        if (lane == 0) W.res[W.maxpos] = c;
-        __syncwarp();
-        uint64_t best = 0;
-        int pos = 0;
-        for (int i = lane; i < ks; i += 32) {
-            const uint64_t v = W.res[i];
-            if (v > best) { best = v; pos = i; }
+    const bool full = W.res_n == ks;
+    if (!full || pos < ks) {
+        // shift [pos, last) up by one, top chunk first, then place c at pos
+        const int last = full ? ks - 1 : W.res_n;
+        for (int c0 = ((last - 1 - pos) / 32) * 32 + pos; c0 >= pos && last > pos; c0 -= 32) {
+            const int i = c0 + lane;
+            const uint64_t v = i < last ? W.res[i] : 0;
+            __syncwarp();
+            if (i < last) W.res[i + 1] = v;
+            __syncwarp();
         }
-        const uint64_t m = warp_max64(best);
-        const unsigned who = __ballot_sync(0xffffffffu, best == m);
-        W.maxpos = __shfl_sync(0xffffffffu, pos, __ffs(who) - 1);
-        W.maxkey = m;
+        if (lane == 0) W.res[pos] = c;
+        if (!full) ++W.res_n;
+        __syncwarp();
     }
-    W.r2 = key_d2(W.maxkey);
+    if (full) {
+        W.trimmed = true;
+        W.r2 = key_d2(W.res[ks - 1]);
+    }
 }
 
 // Remove pool entries above the current admission radius; returns the new size.
@@ -320,6 +318,7 @@ __device__ int pool_compact(WarpState& W, float thr, int lane) {
 // Sort R ascending (bitonic over kcap entries, padded with the empty key) and write the first k.
 __device__ void finish_query(const Params& P, WarpState& W, int q, const float* qv, int status, int tier,
                              int lane) {
+    // R is sorted already; a re-rank replaces its distances and sorts again.
     if (P.rerank) {
         // Re-rank: replace the reduced-precision distances by exact float32 ones.
         for (int i = lane; i < W.res_n; i += 32) {
@@ -330,7 +329,7 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
     }
     for (int i = W.res_n + lane; i < P.kcap; i += 32) W.res[i] = kEmptyKey;
     __syncwarp();
-    for (int size = 2; size <= P.kcap; size <<= 1) {
+    for (int size = 2; P.rerank && size <= P.kcap; size <<= 1) {
         for (int stride = size >> 1; stride; stride >>= 1) {
             for (int t = lane; t < P.kcap / 2; t += 32) {
                 const int lo = 2 * t - (t & (stride - 1));
@@ -361,7 +360,7 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
 
 // One query. Returns false if the fast tier overflowed (nothing written).
 template <class Rows, int G, int CPL, bool DEVICE_TIER>
-__device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int lane) {
+__device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int tier, int lane) {
     Engine<Rows, G, CPL> eng;
     const int32_t seed = P.explore ? P.seeds[q] : (P.seeds ? P.seeds[q] : P.entry);
     const bool seed_ok = seed >= 0 && seed < P.n;
@@ -372,7 +371,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     if (seed < 0 || seed >= P.n) {                                  // bad seed / vertex id
         W.res_n = 0;
         W.hops = W.evals = W.pool_hw = 0;
-        finish_query(P, W, q, qv_smem, DEG_EINVAL, DEVICE_TIER ? 1 : 0, lane);
+        finish_query(P, W, q, qv_smem, DEG_EINVAL, tier, lane);
         return true;
     }
     eng.load_query(qv_smem, P.dim, lane);
@@ -388,8 +387,6 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     W.pool_n = W.res_n = 0;
     W.trimmed = false;
     W.r2 = __int_as_float(0x7f800000);
-    W.maxkey = 0;
-    W.maxpos = 0;
     W.hops = W.evals = W.pool_hw = 0;
     __syncwarp();
 
@@ -472,7 +469,11 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
                         if (!DEVICE_TIER) return false;
                     }
                 }
-                if (toS) W.pool[W.pool_n + __popc(sm & ((1u << lane) - 1))] = key;
+                if (toS) {
+                    W.pool[W.pool_n + __popc(sm & ((1u << lane) - 1))] = key;
+                    // its adjacency row is read if it is ever expanded: start pulling it into L2
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
+                }
                 W.pool_n += __popc(sm);
                 W.pool_hw = max(W.pool_hw, W.pool_n);
             }
@@ -489,7 +490,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         __syncwarp();
     }
-    finish_query(P, W, q, qv_smem, status, DEVICE_TIER ? 1 : 0, lane);
+    finish_query(P, W, q, qv_smem, status, tier, lane);
     return true;
 }
 
@@ -513,15 +514,24 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_fast_kernel(Params
     W.cd2 = reinterpret_cast<float*>(W.cid + kMaxDegree);
     float* qv = W.cd2 + kMaxDegree;
     W.bitmap = nullptr;
-    W.pcap = P.pcap;
+    const int slot = blockIdx.x * P.wpb + warp;
+    uint64_t* const smem_pool = W.pool;
     for (;;) {
         int q = 0;
         if (lane == 0) q = atomicAdd(P.counters + 2, 1);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= P.nq) break;
-        if (!run_query<Rows, G, CPL, false>(P, W, q, qv, lane)) {
-            if (lane == 0) P.overflow[atomicAdd(P.counters, 1)] = q;
+        W.pool = smem_pool;
+        W.pcap = P.pcap;
+        bool done = run_query<Rows, G, CPL, false>(P, W, q, qv, 0, lane);
+        if (!done && slot < P.islots) {
+            // rerun in device-memory mode: bitmap C, larger pool in this warp's slot
+            W.bitmap = P.ibitmaps + (int64_t)slot * P.words;
+            W.pool = P.ipools + (int64_t)slot * P.ipcap;
+            W.pcap = P.ipcap;
+            done = run_query<Rows, G, CPL, true>(P, W, q, qv, 1, lane);
         }
+        if (!done && lane == 0) P.overflow[atomicAdd(P.counters, 1)] = q;
         __syncwarp();
     }
 }
@@ -549,7 +559,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_device_kernel(Para
         if (lane == 0) t = atomicAdd(P.counters + 1, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= count) break;
-        run_query<Rows, G, CPL, true>(P, W, P.overflow[t], qv, lane);
+        run_query<Rows, G, CPL, true>(P, W, P.overflow[t], qv, 2, lane);
         __syncwarp();
     }
 }
@@ -633,25 +643,38 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         ws.cap_q = nq;
     }
     if (!ws.pools) {
-        // Device-tier slots: a bitmap of n bits, a pool of n + 1 keys and 1024 result keys each.
+        // Second kernel: a bitmap of n bits, a pool of n + 1 keys and 1024 result keys per slot.
         const int64_t words = (ix.n + 127) / 128 * 4;
         const int64_t per_slot = words * 4 + 8 * (ix.n + 1) + 8 * kMaxK;
         int64_t slots = (1ll << 30) / per_slot;     // about 1 GiB of scratch
         slots = std::max<int64_t>(8, std::min<int64_t>(256, slots));
         slots = slots / kWarpsPerBlock * kWarpsPerBlock;
+        // Device mode of the fast kernel: one slot per resident warp (up to 16 warps per SM),
+        // a bitmap and a pool of kInlinePool keys each, within about 1.5 GiB.
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t iper = words * 4 + 8ll * kInlinePool;
+        const int64_t islots = std::max<int64_t>(0, std::min<int64_t>((int64_t)sms * 16, (3ll << 29) / iper));
         if ((e = cudaMalloc(&ws.bitmaps, sizeof(uint32_t) * words * slots)) != cudaSuccess ||
             (e = cudaMalloc(&ws.pools, sizeof(uint64_t) * (ix.n + 1) * slots)) != cudaSuccess ||
-            (e = cudaMalloc(&ws.results, sizeof(uint64_t) * kMaxK * slots)) != cudaSuccess) {
+            (e = cudaMalloc(&ws.results, sizeof(uint64_t) * kMaxK * slots)) != cudaSuccess ||
+            (islots && (e = cudaMalloc(&ws.ibitmaps, sizeof(uint32_t) * words * islots)) != cudaSuccess) ||
+            (islots && (e = cudaMalloc(&ws.ipools, sizeof(uint64_t) * kInlinePool * islots)) != cudaSuccess)) {
             workspace_free(ws);
-            return *why = "device-tier scratch", (int)e;
+            return *why = "device-memory scratch", (int)e;
         }
         ws.slots = (int32_t)slots;
         ws.words = words;
+        ws.islots = (int32_t)islots;
+        ws.ipcap = kInlinePool;
     }
     return 0;
 }
 
 void workspace_free(Workspace& ws) {
+    cudaFree(ws.ibitmaps);
+    cudaFree(ws.ipools);
     cudaFree(ws.counters);
     cudaFree(ws.overflow);
     cudaFree(ws.bitmaps);
@@ -695,7 +718,7 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     while ((1 << hs) < hcap) ++hs;
     P.hcap = hcap;
     P.hshift = 32 - hs;
-    P.pcap = a.queue_cap ? std::max(a.queue_cap, 64) : std::max(256, 2 * P.ks + 2 * ix.degree);
+    P.pcap = a.queue_cap ? std::max(a.queue_cap, 64) : std::max(1024, 2 * P.ks + 2 * ix.degree);
     P.pcap = (P.pcap + 31) / 32 * 32;
     P.ids = a.ids;
     P.dists = a.dists;
@@ -707,6 +730,10 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.pools = ws.pools;
     P.results = ws.results;
     P.words = ws.words;
+    P.ibitmaps = ws.ibitmaps;
+    P.ipools = ws.ipools;
+    P.islots = ws.islots;
+    P.ipcap = ws.ipcap;
     if (a.precision == DEG_F32) {
         P.rows = reinterpret_cast<const uint8_t*>(ix.x32);
         P.row_bytes = 4ll * ix.dim_pad;

@@ -170,6 +170,24 @@ DEG_API deg_status deg_search_host(deg_index* idx, const deg_search_params* p, c
 DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
                      int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
 
+/* knn_exact without any device allocation. The paper has no counterpart: this is a library
+ * service for callers that cannot allocate device memory while they run -- for instance a
+ * process whose device memory is entirely reserved by another allocator (a framework's caching
+ * allocator, a fixed memory budget), or a loop that cannot accept the device-wide
+ * synchronisation that cudaMalloc/cudaFree imply. The caller still owns every input and output.
+ * Same arguments, results and errors as knn_exact, except:
+ *  - the distances live in one static device array of 32 MiB (8,388,608 float32) held by every
+ *    GPU that loads the library until the process exits; n must be at most 8,388,608 (else
+ *    DEG_EINVAL) and queries are processed in chunks of 8,388,608 / n;
+ *  - the first call on a device looks up that array's device address (cudaGetSymbolAddress, with
+ *    the device current) and caches it: make that first call before any stream capture;
+ *  - all calls share the array and it keeps the last call's contents; two calls whose work
+ *    overlaps on the GPU (different streams, or different host threads) race on it and give
+ *    undefined results: order them on one stream or synchronise between them;
+ *  - the call does not synchronise the stream (knn_exact does). */
+DEG_API deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
+                                     int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 DEG_API const char* deg_last_error(void);
 

@@ -74,6 +74,7 @@ def lib() -> ctypes.CDLL:
             "deg_search_ex": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P, P, P]),
             "deg_search_host": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P]),
             "knn_exact": (S, [P, i64, P, i64, i32, i32, P, P, P]),
+            "knn_exact_noalloc": (S, [P, i64, P, i64, i32, i32, P, P, P]),
             "deg_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():

@@ -427,3 +427,19 @@ extern "C" deg_status knn_exact(const float* base_dev, int64_t n, const float* q
     if (e != 0) return fail(DEG_ECUDA, "knn_exact: " + why);
     return DEG_OK;
 }
+
+extern "C" deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
+                                        int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream) {
+    if (n <= 0 || n > INT32_MAX || nq < 0 || nq > INT32_MAX || dim <= 0)
+        return fail(DEG_EINVAL, "knn_exact_noalloc: bad sizes");
+    if (k < 1 || k > 256) return fail(DEG_EINVAL, "knn_exact_noalloc: k must be in [1, 256]");
+    if (k > n) return fail(DEG_EINVAL, "knn_exact_noalloc: k larger than n");
+    if (n > (8ll << 20)) return fail(DEG_EINVAL, "knn_exact_noalloc: n exceeds the static scratch (at most 8388608 base rows)");
+    if (nq == 0) return DEG_OK;
+    if (!base_dev || !queries_dev || !ids_dev || !dists_dev) return fail(DEG_EINVAL, "knn_exact_noalloc: NULL argument");
+    std::string why;
+    const int e = launch_knn_exact_noalloc(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
+                                           static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "knn_exact_noalloc: " + why);
+    return DEG_OK;
+}

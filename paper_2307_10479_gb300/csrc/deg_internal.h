@@ -92,6 +92,9 @@ int make_fp8_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 // Exact kNN (knn_exact.cu).
 int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
                      int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
+// Same, on a fixed statically allocated scratch (no allocation in the call).
+int launch_knn_exact_noalloc(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
+                             int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
 
 }  // namespace deg
 

@@ -156,3 +156,58 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
 }
 
 }  // namespace deg
+
+// ---- knn_exact_noalloc: the same two kernels on a fixed, statically allocated scratch --------
+// For callers that cannot allocate device memory during the call. The distance buffer is a
+// file-scope __device__ array (32 MiB), so every GPU that loads the library holds it until the
+// process exits. Host code cannot use the array's name as a device address: the first call on a
+// device looks the address up with cudaGetSymbolAddress (that device current) and caches it.
+#include <mutex>
+
+namespace deg {
+namespace {
+
+constexpr int64_t kNoAllocScratchFloats = 8ll << 20;                 // 32 MiB of float32 distances
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+int64_t knn_noalloc_capacity() { return kNoAllocScratchFloats; }
+
+int launch_knn_exact_noalloc(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
+                             int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (n > kNoAllocScratchFloats)
+        return *why = "n exceeds the static scratch (at most 8388608 base rows)", (int)cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
+    if (dev < 0 || dev >= kMaxDevices) return *why = "device index above 63", (int)cudaErrorInvalidValue;
+    float* D = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e), (int)e;
+            g_noalloc_ptr[dev] = static_cast<float*>(p);
+        }
+        D = g_noalloc_ptr[dev];
+    }
+    // Every distance a chunk reads is written first by the same chunk: nothing needs clearing.
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, kNoAllocScratchFloats / n));
+    for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
+        const int64_t qc = std::min(chunk, nq - q0);
+        const dim3 grid((unsigned)((n + kTile - 1) / kTile), (unsigned)((qc + kTile - 1) / kTile));
+        dist_tile_kernel<<<grid, 256, 0, st>>>(queries + q0 * dim, qc, base, n, dim, D);
+        select_topk_kernel<<<(unsigned)qc, kSelThreads, 0, st>>>(D, n, k, ids + q0 * k, dists + q0 * k);
+        if ((e = cudaGetLastError()) != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
+    }
+    return 0;
+}
+
+}  // namespace deg

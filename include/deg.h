@@ -126,16 +126,18 @@ typedef struct {
                              re-rank them on the float32 rows; 0 = k (no widening)           */
     int32_t max_hops;     /* 0 = unlimited; else a query stops after this many expansions and
                              reports DEG_EHOPLIMIT with its current result list               */
-    int32_t visited_cap;  /* on-chip visited-set slots per query (power of two), 0 = auto     */
-    int32_t queue_cap;    /* on-chip candidate slots per query, 0 = auto                      */
+    int32_t visited_cap;  /* reserved, must be 0 (the checked set is an n-bit bitmap)          */
+    int32_t queue_cap;    /* candidates a query may hold in its device-memory pool in the
+                             main kernel, 0 = 32768 (the maximum); a query needing more is
+                             finished by a second kernel with room for all n vertices          */
 } deg_search_params;
 
 /* Plain search: one Alg. 1 run per query q of queries_dev [nq][dim] float32, seeded at
  * seeds_dev[q] (int32, nullable: NULL = the entry vertex of deg_upload). Seeds enter the result
- * list (Alg. 1 line "R <- S"). Writes ids_dev [nq][k] int32 and dists_dev [nq][k] float32;
- * status_dev (nullable) [nq] int32 gets DEG_OK or a per-query status. Exact: a query whose
- * on-chip visited set or candidate queue would overflow is finished by a second kernel that
- * keeps its state in device memory, with an identical result. */
+ * list (Alg. 1 initialises R with the seeds). Writes ids_dev [nq][k] int32 and dists_dev
+ * [nq][k] float32; status_dev (nullable) [nq] int32 gets DEG_OK or a per-query status. Exact: a
+ * query whose candidate pool outgrows its slot is finished by a second kernel with room for all
+ * n vertices, with an identical result. */
 DEG_API deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
                       const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
                       int32_t* status_dev, void* stream);
@@ -148,8 +150,8 @@ DEG_API deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, in
 
 /* Full form of both. queries_dev is NULL iff explore != 0 (then seeds_dev holds the vertex
  * ids). trace_dev (nullable) [nq][4] int32 receives per query: hops H (expansions), vertices
- * evaluated E (= |C|), the candidate-queue high-water mark, and 1 if the query was finished by
- * the device-memory kernel. */
+ * evaluated E (= |C|), the largest size of the candidate set S, and 1 if the query was
+ * finished by the second kernel. */
 DEG_API deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, const float* queries_dev,
                          const int32_t* seeds_dev, int32_t explore, int64_t nq, int32_t* ids_dev,
                          float* dists_dev, int32_t* status_dev, int32_t* trace_dev, void* stream);

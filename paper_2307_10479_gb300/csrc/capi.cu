@@ -85,6 +85,8 @@ void free_device(deg_index* idx) {
     cudaFree(d.x8);
     cudaFree(d.scale8);
     cudaFree(d.adj);
+    cudaFree(d.old2new);
+    cudaFree(d.new2old);
     d = DeviceIndex{};
     workspace_free(idx->ws);
     idx->uploaded_mask = 0;
@@ -278,6 +280,10 @@ extern "C" deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* s
             free_device(idx);
             return fail(DEG_ECUDA, "deg_upload: entry vertex: " + why);
         }
+        if (apply_locality_layout(d, st, &why) != 0) {
+            free_device(idx);
+            return fail(DEG_ECUDA, "deg_upload: layout: " + why);
+        }
     }
     if ((precision_mask & (1 << DEG_BF16)) && !d.xbf) {
         if (make_bf16_copy(d, st, &why) != 0) return fail(DEG_ECUDA, "deg_upload: bf16 copy: " + why);
@@ -296,20 +302,35 @@ extern "C" int32_t deg_entry_vertex(const deg_index* idx) { return idx ? idx->de
 extern "C" deg_status deg_export_codes(const deg_index* idx, int32_t precision, void* codes_host, float* scales_host) {
     if (!idx || !codes_host) return fail(DEG_EINVAL, "deg_export_codes: NULL argument");
     const DeviceIndex& d = idx->dev;
-    cudaError_t e;
-    if (precision == DEG_BF16) {
-        if (!d.xbf) return fail(DEG_ENOTREADY, "deg_export_codes: bf16 copy not uploaded");
-        e = cudaMemcpy2D(codes_host, 2 * (size_t)d.dim, d.xbf, 2 * (size_t)d.dim_pad16, 2 * (size_t)d.dim, d.n,
-                         cudaMemcpyDeviceToHost);
-    } else if (precision == DEG_FP8) {
-        if (!d.x8) return fail(DEG_ENOTREADY, "deg_export_codes: fp8 copy not uploaded");
-        if (!scales_host) return fail(DEG_EINVAL, "deg_export_codes: scales_host is NULL");
-        e = cudaMemcpy2D(codes_host, (size_t)d.dim, d.x8, (size_t)d.dim_pad8, (size_t)d.dim, d.n, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess) e = cudaMemcpy(scales_host, d.scale8, sizeof(float) * d.n, cudaMemcpyDeviceToHost);
-    } else {
+    if (precision != DEG_BF16 && precision != DEG_FP8)
         return fail(DEG_EINVAL, "deg_export_codes: precision must be DEG_BF16 or DEG_FP8");
+    if (precision == DEG_BF16 ? !d.xbf : !d.x8) return fail(DEG_ENOTREADY, "deg_export_codes: copy not uploaded");
+    if (precision == DEG_FP8 && !scales_host) return fail(DEG_EINVAL, "deg_export_codes: scales_host is NULL");
+    // The device stores rows in internal (layout) order: copy them out, then put them back in the
+    // caller's order.
+    const size_t eb = precision == DEG_BF16 ? 2 : 1;
+    std::vector<uint8_t> rows;
+    std::vector<float> sc;
+    std::vector<int32_t> o2n;
+    try {
+        rows.resize(eb * d.dim * d.n);
+        o2n.resize(d.n);
+        if (precision == DEG_FP8) sc.resize(d.n);
+    } catch (const std::bad_alloc&) {
+        return fail(DEG_ENOMEM, "deg_export_codes: host allocation failed");
     }
-    return e == cudaSuccess ? DEG_OK : cuda_fail(e, "deg_export_codes");
+    cudaError_t e = precision == DEG_BF16
+        ? cudaMemcpy2D(rows.data(), eb * d.dim, d.xbf, 2 * (size_t)d.dim_pad16, eb * d.dim, d.n, cudaMemcpyDeviceToHost)
+        : cudaMemcpy2D(rows.data(), eb * d.dim, d.x8, (size_t)d.dim_pad8, eb * d.dim, d.n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(o2n.data(), d.old2new, 4 * d.n, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && precision == DEG_FP8) e = cudaMemcpy(sc.data(), d.scale8, 4 * d.n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "deg_export_codes");
+    uint8_t* out = static_cast<uint8_t*>(codes_host);
+    for (int64_t v = 0; v < d.n; ++v) {
+        std::memcpy(out + v * eb * d.dim, rows.data() + (size_t)o2n[v] * eb * d.dim, eb * d.dim);
+        if (precision == DEG_FP8) scales_host[v] = sc[o2n[v]];
+    }
+    return DEG_OK;
 }
 
 extern "C" void deg_free(deg_index* idx) {
@@ -333,9 +354,8 @@ deg_status validate_search(const deg_index* idx, const deg_search_params* p, con
     if (p->rerank < 0 || p->rerank > 1024 || (p->rerank && p->rerank < p->k))
         return fail(DEG_EINVAL, "search: rerank must be 0 or in [k, 1024]");
     if (p->max_hops < 0) return fail(DEG_EINVAL, "search: max_hops must be >= 0");
-    if (p->visited_cap < 0 || (p->visited_cap & (p->visited_cap - 1)) || p->visited_cap > (1 << 16))
-        return fail(DEG_EINVAL, "search: visited_cap must be 0 or a power of two <= 65536");
-    if (p->queue_cap < 0 || p->queue_cap > (1 << 14)) return fail(DEG_EINVAL, "search: queue_cap out of range");
+    if (p->visited_cap != 0) return fail(DEG_EINVAL, "search: visited_cap is reserved and must be 0");
+    if (p->queue_cap < 0 || p->queue_cap > 32768) return fail(DEG_EINVAL, "search: queue_cap must be in [0, 32768]");
     if (explore ? (queries != nullptr || seeds == nullptr) : (queries == nullptr && nq > 0))
         return fail(DEG_EINVAL, "search: explore needs vertex ids and no query vectors; search needs vectors");
     return DEG_OK;

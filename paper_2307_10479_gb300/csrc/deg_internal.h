@@ -33,24 +33,28 @@ struct DeviceIndex {
     uint8_t* x8 = nullptr;    // [n][dim_pad8] E4M3 codes (optional)
     float* scale8 = nullptr;  // [n] per-row scale of the E4M3 codes
     int32_t dim_pad8 = 0;     // fp8 row stride (multiple of 16)
-    int32_t* adj = nullptr;   // [n][deg_pad], padded slots = -1
-    int32_t entry = -1;
+    int32_t* adj = nullptr;   // [n][deg_pad], padded slots = -1 (internal ids)
+    int32_t entry = -1;       // entry vertex, caller's id
+    // Locality layout: rows and adjacency are stored in internal-id order (layout.cu).
+    int32_t* old2new = nullptr;   // [n] caller id -> internal id
+    int32_t* new2old = nullptr;   // [n] internal id -> caller id
+    int32_t entry_internal = -1;
 };
 
-// Scratch for one search call: the overflow list, and the per-slot device-memory state of the
-// second (device-memory) kernel.
+// Scratch of the search kernels: the overflow list, and per-warp device-memory state (a visited
+// bitmap of n bits and a back pool of candidate keys) for the main kernel and, with room for all
+// n vertices, for the second kernel.
 struct Workspace {
-    int32_t* counters = nullptr;     // [0] overflow count, [1] work cursor of the 2nd kernel
+    int32_t* counters = nullptr;     // [0] overflow count, [1] second-kernel cursor, [2] main cursor
     int32_t* overflow = nullptr;     // [cap_q] query indices
     int64_t cap_q = 0;
     int64_t words = 0;               // 32-bit words of one visited bitmap
-    uint32_t* ibitmaps = nullptr;    // device mode of the fast kernel: [islots][words]
-    uint64_t* ipools = nullptr;      //   [islots][ipcap] candidate keys
-    int32_t islots = 0, ipcap = 0;
-    uint32_t* bitmaps = nullptr;     // second kernel: [slots][words] visited bitmaps
-    uint64_t* pools = nullptr;       //   [slots][n + 1] candidate keys
-    uint64_t* results = nullptr;     //   [slots][1024] result keys
-    int32_t slots = 0;
+    uint32_t* bitmaps = nullptr;     // main kernel: [slots][words]
+    uint64_t* backs = nullptr;       //   [slots][bcap] candidate keys
+    int32_t slots = 0, bcap = 0;
+    uint32_t* pbitmaps = nullptr;    // second kernel: [pslots][words]
+    uint64_t* pbacks = nullptr;      //   [pslots][n + 1]
+    int32_t pslots = 0;
     // host e2e staging
     void* dq = nullptr;
     void* did = nullptr;
@@ -84,6 +88,9 @@ void workspace_free(Workspace& ws);
 
 // Entry vertex (entry.cu): lower median per coordinate, then the nearest row. Synchronous.
 int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+
+// Reorder rows and adjacency by nearest pivot (layout.cu); fills old2new/new2old. Synchronous.
+int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);

@@ -1,0 +1,209 @@
+// Locality layout of an uploaded index (not part of the paper's method; a device-memory layout).
+//
+// Vertices get new internal ids so that vectors near each other in space get nearby ids: P
+// pivot rows (every (n/P)-th vertex) are chosen, every vertex is labelled with its nearest
+// pivot (float32 L2, ties -> lower pivot index), and vertices are ordered by (label, original
+// id) with a deterministic counting sort. Rows and the adjacency are then stored in that order.
+// A query's visited bitmap words, its rows and its adjacency rows then cluster in a few address
+// ranges, which keeps them in L2. Searches map caller ids in (seeds, exploration vertices) and
+// result ids out, so the layout is invisible to callers; the search keys order ties by internal
+// id.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "deg_internal.h"
+
+namespace deg {
+namespace {
+
+constexpr int kTile = 64, kKc = 32, kChunk = 1024;
+
+// labels[v] = argmin_p |x_v - x_{pivot p}|^2 (ties -> lower p). 64 rows x 64 pivots per tile.
+__global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restrict__ x, int64_t n, int32_t dim,
+                                                            int32_t dim_pad, const int32_t* __restrict__ pivots,
+                                                            int32_t np, int32_t* __restrict__ labels) {
+    __shared__ float xs[kKc][kTile + 4];
+    __shared__ float ps[kKc][kTile + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = (int64_t)blockIdx.x * kTile;
+    unsigned long long best[4] = {~0ull, ~0ull, ~0ull, ~0ull};
+    for (int p0 = 0; p0 < np; p0 += kTile) {
+        float acc[4][4] = {};
+        for (int k0 = 0; k0 < dim; k0 += kKc) {
+            for (int t = threadIdx.x; t < kTile * kKc; t += 256) {
+                const int r = t / kKc, c = t % kKc;
+                const bool kc = k0 + c < dim;
+                xs[c][r] = (kc && r0 + r < n) ? x[(r0 + r) * dim_pad + k0 + c] : 0.f;
+                ps[c][r] = (kc && p0 + r < np) ? x[(int64_t)pivots[p0 + r] * dim_pad + k0 + c] : 0.f;
+            }
+            __syncthreads();
+#pragma unroll 8
+            for (int c = 0; c < kKc; ++c) {
+                float a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) a[i] = xs[c][ty + 16 * i];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) b[j] = ps[c][tx + 16 * j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float t = a[i] - b[j];
+                        acc[i][j] = fmaf(t, t, acc[i][j]);
+                    }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = p0 + tx + 16 * j;
+                if (p < np) best[i] = min(best[i], ((unsigned long long)__float_as_uint(acc[i][j]) << 32) | (uint32_t)p);
+            }
+    }
+    // reduce over the 16 threads sharing a row (same ty, lanes differ in tx)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        unsigned long long v = best[i];
+#pragma unroll
+        for (int m = 8; m; m >>= 1) {
+            const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+            const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+            v = min(v, ((unsigned long long)hi << 32) | lo);
+        }
+        const int64_t r = r0 + ty + 16 * i;
+        if (tx == 0 && r < n) labels[r] = (int32_t)(uint32_t)v;
+    }
+}
+
+// Per chunk of kChunk vertices: how many carry each label.
+__global__ void chunk_hist_kernel(const int32_t* labels, int64_t n, int32_t np, int32_t* chunk_hist) {
+    extern __shared__ int32_t h[];
+    for (int i = threadIdx.x; i < np; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t lo = (int64_t)blockIdx.x * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+    for (int64_t v = lo + threadIdx.x; v < hi; v += blockDim.x) atomicAdd(h + labels[v], 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < np; i += blockDim.x) chunk_hist[(int64_t)blockIdx.x * np + i] = h[i];
+}
+
+// For each label: totals, and the running count before each chunk (in place).
+__global__ void label_scan_kernel(int32_t* chunk_hist, int64_t nchunks, int32_t np, int32_t* totals) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= np) return;
+    int32_t run = 0;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int32_t t = chunk_hist[c * np + l];
+        chunk_hist[c * np + l] = run;
+        run += t;
+    }
+    totals[l] = run;
+}
+
+// Exclusive scan of the label totals (one block).
+__global__ void offsets_kernel(const int32_t* totals, int32_t np, int32_t* offsets) {
+    if (threadIdx.x == 0) {
+        int32_t run = 0;
+        for (int l = 0; l < np; ++l) {
+            offsets[l] = run;
+            run += totals[l];
+        }
+    }
+}
+
+// New id of every vertex: label offset + earlier chunks' count + rank inside the chunk.
+__global__ void scatter_ids_kernel(const int32_t* labels, int64_t n, int32_t np, const int32_t* chunk_before,
+                                   const int32_t* offsets, int32_t* old2new, int32_t* new2old) {
+    __shared__ int32_t lab[kChunk];
+    const int64_t lo = (int64_t)blockIdx.x * kChunk, hi = lo + kChunk < n ? lo + kChunk : n;
+    const int cnt = (int)(hi - lo);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) lab[i] = labels[lo + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int32_t l = lab[i];
+        int rank = 0;
+        for (int u = 0; u < i; ++u) rank += (lab[u] == l);
+        const int32_t pos = offsets[l] + chunk_before[(int64_t)blockIdx.x * np + l] + rank;
+        old2new[lo + i] = pos;
+        new2old[pos] = (int32_t)(lo + i);
+    }
+}
+
+__global__ void permute_rows_kernel(const float4* src, float4* dst, int64_t n, int32_t row4, const int32_t* new2old) {
+    const int64_t total = n * row4;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / row4;
+        const int c = (int)(t - p * row4);
+        dst[t] = src[(int64_t)new2old[p] * row4 + c];
+    }
+}
+
+__global__ void permute_adj_kernel(const int32_t* src, int32_t* dst, int64_t n, int32_t deg_pad, int32_t degree,
+                                   const int32_t* new2old, const int32_t* old2new) {
+    const int64_t total = n * deg_pad;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = t / deg_pad;
+        const int j = (int)(t - p * deg_pad);
+        dst[t] = j < degree ? old2new[src[(int64_t)new2old[p] * deg_pad + j]] : -1;
+    }
+}
+
+__global__ void pivot_ids_kernel(int32_t* pivots, int32_t np, int64_t stride) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < np) pivots[p] = (int32_t)(p * stride);
+}
+
+}  // namespace
+
+int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = ix.n;
+    const int32_t np = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, n / 256));
+    const int64_t nchunks = (n + kChunk - 1) / kChunk;
+    int32_t *pivots = nullptr, *labels = nullptr, *chunk_hist = nullptr, *totals = nullptr, *offsets = nullptr;
+    float* x2 = nullptr;
+    int32_t* adj2 = nullptr;
+    cudaError_t e;
+    auto cleanup = [&]() {
+        cudaFree(pivots); cudaFree(labels); cudaFree(chunk_hist); cudaFree(totals); cudaFree(offsets);
+        cudaFree(x2); cudaFree(adj2);
+    };
+    if ((e = cudaMalloc(&pivots, 4 * np)) != cudaSuccess || (e = cudaMalloc(&labels, 4 * n)) != cudaSuccess ||
+        (e = cudaMalloc(&chunk_hist, 4 * nchunks * np)) != cudaSuccess || (e = cudaMalloc(&totals, 4 * np)) != cudaSuccess ||
+        (e = cudaMalloc(&offsets, 4 * np)) != cudaSuccess || (e = cudaMalloc(&ix.old2new, 4 * n)) != cudaSuccess ||
+        (e = cudaMalloc(&ix.new2old, 4 * n)) != cudaSuccess ||
+        (e = cudaMalloc(&x2, sizeof(float) * n * ix.dim_pad)) != cudaSuccess ||
+        (e = cudaMalloc(&adj2, sizeof(int32_t) * n * ix.deg_pad)) != cudaSuccess) {
+        cleanup();
+        return *why = std::string("layout buffers: ") + cudaGetErrorString(e), (int)e;
+    }
+    pivot_ids_kernel<<<(np + 255) / 256, 256, 0, st>>>(pivots, np, n / np);
+    nearest_pivot_kernel<<<(unsigned)((n + kTile - 1) / kTile), 256, 0, st>>>(ix.x32, n, ix.dim, ix.dim_pad, pivots, np, labels);
+    chunk_hist_kernel<<<(unsigned)nchunks, 256, 4 * np, st>>>(labels, n, np, chunk_hist);
+    label_scan_kernel<<<(np + 127) / 128, 128, 0, st>>>(chunk_hist, nchunks, np, totals);
+    offsets_kernel<<<1, 32, 0, st>>>(totals, np, offsets);
+    scatter_ids_kernel<<<(unsigned)nchunks, 256, 0, st>>>(labels, n, np, chunk_hist, offsets, ix.old2new, ix.new2old);
+    permute_rows_kernel<<<4096, 256, 0, st>>>(reinterpret_cast<const float4*>(ix.x32), reinterpret_cast<float4*>(x2), n,
+                                              ix.dim_pad / 4, ix.new2old);
+    permute_adj_kernel<<<4096, 256, 0, st>>>(ix.adj, adj2, n, ix.deg_pad, ix.degree, ix.new2old, ix.old2new);
+    if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cleanup();
+        return *why = std::string("layout kernels: ") + cudaGetErrorString(e), (int)e;
+    }
+    std::swap(ix.x32, x2);
+    std::swap(ix.adj, adj2);
+    int32_t entry_new = -1;
+    if ((e = cudaMemcpy(&entry_new, ix.old2new + ix.entry, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+        cleanup();
+        return *why = cudaGetErrorString(e), (int)e;
+    }
+    ix.entry_internal = entry_new;
+    cleanup();  // frees the old rows and adjacency (swapped into x2 / adj2) and the scratch
+    return 0;
+}
+
+}  // namespace deg

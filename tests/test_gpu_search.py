@@ -67,15 +67,16 @@ def test_explicit_seeds_parity(cfg1):
     compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d)
 
 
-def test_device_memory_tier_is_bit_identical(cfg1):
-    # A 64-slot visited table overflows on every query; the device-memory kernel reruns them.
+def test_second_kernel_is_bit_identical(cfg1):
+    # A one-key device-memory pool overflows on every query that needs it; those queries are
+    # rerun from scratch by the second kernel (room for all n vertices). Same results, same H, E.
     idx = cfg1["idx"]
-    a_ids, a_d, a_tr = idx.search(cfg1["qd"], k=10, eps=0.1, with_trace=True)
-    b_ids, b_d, b_tr = idx.search(cfg1["qd"], k=10, eps=0.1, visited_cap=64, with_trace=True)
+    a_ids, a_d, a_tr = idx.search(cfg1["qd"], k=10, eps=0.2, with_trace=True)
+    b_ids, b_d, b_tr = idx.search(cfg1["qd"], k=10, eps=0.2, queue_cap=1, with_trace=True)
     torch.cuda.synchronize()
-    assert (b_tr[:, 3] == 1).all() and (a_tr[:, 3] == 0).float().mean() > 0.9
+    assert (a_tr[:, 3] == 0).all() and (b_tr[:, 3] == 1).sum() > 100
     assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
-    assert torch.equal(a_tr[:, :2], b_tr[:, :2])
+    assert torch.equal(a_tr[:, :2], b_tr[:, :2])       # the pool peak depends on the capacity
 
 
 def test_huge_eps_returns_exact_knn(cfg1):

@@ -135,16 +135,28 @@ def algorithmic_bytes(trace, dim, degree, k, row_bytes):
     return int((dim * 4 + H * degree * 4 + E * row_bytes + k * 8).sum())
 
 
-def pick_eps(idx, qd, gt, precision="f32", rerank=0):
+def pick_eps(idx, qd, gt, **form):
+    """Smallest eps of the grid whose recall@10 reaches the target, for one search form."""
     import torch
     for eps in EPS_GRID:
-        ids, _ = idx.search(qd, k=K, eps=eps, precision=precision, rerank=rerank)
+        ids, _ = idx.search(qd, k=K, eps=eps, **form)
         torch.cuda.synchronize()
         r = recall(ids.cpu().numpy(), gt)
-        log(f"  eps {eps:.2f}: recall@10 {r:.4f}")
+        log(f"  {form}: eps {eps:.2f}: recall@10 {r:.4f}")
         if r >= TARGET_RECALL:
             return eps, r
     return EPS_GRID[-1], r
+
+
+# Search forms measured: the paper's plain search (float32 rows, fixed entry vertex) and the
+# library's fast forms (entry routed to the nearest pivot; reduced-precision rows + re-rank).
+FORMS = {
+    "plain float32, fixed entry": dict(precision="f32", entry="fixed"),
+    "float32, pivot entry": dict(precision="f32", entry="pivot"),
+    "bf16 + re-rank 32, pivot entry": dict(precision="bf16", rerank=32, entry="pivot"),
+    "fp8 + re-rank 32, pivot entry": dict(precision="fp8", rerank=32, entry="pivot"),
+}
+ROW_BYTES = {"f32": 512, "bf16": 256, "fp8": 128 + 4}
 
 
 def time_steps(fn, steps, warmup, stream):
@@ -231,7 +243,7 @@ def run_reference(args, rank):
 
 # eps at which the plain float32 search reaches recall@10 >= 0.95 on this workload (from the
 # sweep the GPU arm runs at start-up; the reference arm uses it so both arms do the same work)
-OPERATING_EPS = 0.1
+OPERATING_EPS = 0.08
 
 
 def main():
@@ -264,86 +276,110 @@ def main():
     t0 = time.time()
     base, q = w.base(), w.queries()
     idx = graphs.load_or_build(w, base)
-    idx.upload(("f32",))
+    idx.upload(("f32", "bf16", "fp8"))
     n, dim, degree = idx.info()
     log(f"[bench] index {n} x {dim}, d={degree}, entry {idx.entry_vertex}, setup {time.time() - t0:.1f} s")
     qd = torch.from_numpy(q).cuda()
     gt_ids, _ = deg.knn_exact(torch.from_numpy(base).cuda(), qd, K)
     gt = gt_ids.cpu().numpy()
     torch.cuda.empty_cache()
-    if args.eps is None:
-        eps, rec = pick_eps(idx, qd, gt)
-    else:
-        eps = args.eps
-        ids, _ = idx.search(qd, k=K, eps=eps)
-        rec = recall(ids.cpu().numpy(), gt)
-    # trace pass (untimed): hops and evaluations per query for the algorithmic byte count
-    _, _, st, tr = idx.search(qd, k=K, eps=eps, with_status=True, with_trace=True)
-    trace = tr.cpu().numpy()
-    assert (st.cpu().numpy() == 0).all()
-    alg_bytes = algorithmic_bytes(trace, dim, degree, K, 4 * ((dim + 3) // 4 * 4))
     stream = torch.cuda.current_stream()
     out = (torch.empty((len(q), K), dtype=torch.int32, device="cuda"),
            torch.empty((len(q), K), dtype=torch.float32, device="cuda"))
 
-    def step():
-        idx.search(qd, k=K, eps=eps, out=out)
+    def measure(name, form, steps, warmup, clocks=None):
+        if args.eps is not None:
+            eps = args.eps
+            ids, _ = idx.search(qd, k=K, eps=eps, **form)
+            rec = recall(ids.cpu().numpy(), gt)
+        else:
+            eps, rec = pick_eps(idx, qd, gt, **form)
+        _, _, st, tr = idx.search(qd, k=K, eps=eps, with_status=True, with_trace=True, **form)
+        trace = tr.cpu().numpy()
+        assert (st.cpu().numpy() == 0).all()
+        rb = ROW_BYTES[form.get("precision", "f32")]
+        alg = algorithmic_bytes(trace, dim, degree, K, rb)
+        if form.get("rerank"):
+            alg += len(q) * form["rerank"] * dim * 4          # re-rank reads float32 rows
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        ms = time_steps(lambda: idx.search(qd, k=K, eps=eps, out=out, **form), steps, warmup, stream)
+        clk = clocks.stop() if clocks else None
+        total = sum(ms)
+        if dist:
+            t = torch.tensor([total], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        mean_ms = total / steps
+        res = {"qps": world * len(q) * steps / (total / 1e3), "eps": eps, "recall_at_10": rec, "ms_per_step": mean_ms,
+               "p50_ms": sorted(ms)[len(ms) // 2], "p99_ms": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
+               "alg_bytes": alg, "achieved_gbs": alg / (mean_ms / 1e3) / 1e9,
+               "H_mean": float(trace[:, 0].mean()), "H_max": int(trace[:, 0].max()), "E_mean": float(trace[:, 1].mean()),
+               "second_kernel_frac": float(trace[:, 3].mean())}
+        log(f"[bench] {name}: {res['qps']:.0f} QPS at recall {rec:.4f} (eps {eps}), {mean_ms:.2f} ms/step")
+        return res, clk
 
+    forms = {}
     clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    ms = time_steps(step, args.steps, args.warmup, stream)
-    clk = clocks.stop()
-    total_ms = sum(ms)
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    qps = world * len(q) * args.steps / (total_ms / 1e3)
-    step_ms = sorted(ms)
+    plain, _ = measure("plain", FORMS["plain float32, fixed entry"], max(3, args.steps // 4), args.warmup)
+    forms["plain float32, fixed entry"] = plain
+    for name in list(FORMS)[1:]:
+        forms[name], _ = measure(name, FORMS[name], max(3, args.steps // 4), args.warmup)
+    ok = {k: v for k, v in forms.items() if v["recall_at_10"] >= TARGET_RECALL}
+    best = max(ok or forms, key=lambda k: (ok or forms)[k]["qps"])
+    # the headline: the fastest form, timed again over the full step count with clocks sampled
+    head, clk = measure(best, FORMS[best], args.steps, args.warmup, clocks)
+    eps = head["eps"]
 
     # end to end through the C ABI with host buffers (H2D of the queries, D2H of the results)
     qh = torch.from_numpy(q).pin_memory().numpy()
     ih = torch.empty((len(q), K), dtype=torch.int32).pin_memory().numpy()
     dh = torch.empty((len(q), K), dtype=torch.float32).pin_memory().numpy()
+    hform = {k: v for k, v in FORMS[best].items()}
     e2e_steps = max(3, min(args.steps, 50))
     for _ in range(3):
-        idx.search_host(qh, K, eps, out=(ih, dh))
+        idx.search_host(qh, K, eps, out=(ih, dh), **hform)
     t1 = time.perf_counter()
     for _ in range(e2e_steps):
-        idx.search_host(qh, K, eps, out=(ih, dh))
+        idx.search_host(qh, K, eps, out=(ih, dh), **hform)
     e2e_s = (time.perf_counter() - t1) / e2e_steps
-    e2e_ok = recall(ih, gt) >= TARGET_RECALL - 1e-9 or rec < TARGET_RECALL
+    e2e_rec = recall(ih, gt)
 
     peak, peak_kind = measured_peak()
-    mean_ms = total_ms / args.steps
-    achieved = alg_bytes / (mean_ms / 1e3) / 1e9
+
+    def roofline(r, kernel, traffic):
+        return {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+                "alg_bytes_per_launch": r["alg_bytes"],
+                "per_query": {"H_mean": r["H_mean"], "H_max": r["H_max"], "E_mean": r["E_mean"],
+                              "second_kernel_frac": r["second_kernel_frac"]}}
+
+    kname = {"f32": "F32Rows, 32 lanes/row", "bf16": "BF16Rows, 16 lanes/row", "fp8": "FP8Rows, 8 lanes/row"}
     line = {
-        "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "metric": METRIC, "value": head["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if FORMS[best]["precision"] == "f32" else FORMS[best]["precision"],
+        "data": "synthetic",
         "config": {"workload": w.name, "n": n, "dim": dim, "degree": degree, "queries_per_step": len(q), "k": K,
-                   "eps": eps, "recall_at_10": rec, "form": "plain float32 search",
+                   "eps": eps, "recall_at_10": head["recall_at_10"], "form": best,
                    "parallelism": f"replicas x{world}", "l2": "index 512 MB rows + 128 MB graph > 129 MB L2; no flush"},
-        "latency_ms": {"p50": step_ms[len(step_ms) // 2], "p99": step_ms[min(len(step_ms) - 1, int(0.99 * len(step_ms)))],
-                       "what": "whole 10k-query batch per step"},
-        "hbm_gbs": achieved,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(), "peak_kind": peak_kind,
-                     "kernel": "search_fast_kernel (F32 rows, 32 lanes/row)",
-                     "alg_bytes_per_launch": alg_bytes,
-                     "per_query": {"H_mean": float(trace[:, 0].mean()), "E_mean": float(trace[:, 1].mean()),
-                                   "device_tier_frac": float(trace[:, 3].mean())}},
+        "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "what": "whole 10k-query batch per step"},
+        "hbm_gbs": head["achieved_gbs"],
+        "vs_plain_fp32": head["qps"] / plain["qps"],
+        "forms": forms,
+        "roofline": roofline(head, f"search_fast_kernel ({kname[FORMS[best]['precision']]})", None),
+        "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)", recorded_traffic()),
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
-                "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_ok": bool(e2e_ok)},
-        "gpu_launches": 2 * args.steps,
+                "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},
+        "gpu_launches": (4 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
-        line["cpu_baseline"] = cpu_baseline(base, idx.adjacency(), q, oracle.median_vertex(base), eps)
+        line["cpu_baseline"] = cpu_baseline(base, idx.adjacency(), q, oracle.median_vertex(base), plain["eps"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

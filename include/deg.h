@@ -130,6 +130,9 @@ typedef struct {
     int32_t queue_cap;    /* candidates a query may hold in its device-memory pool in the
                              main kernel, 0 = 32768 (the maximum); a query needing more is
                              finished by a second kernel with room for all n vertices          */
+    int32_t entry_mode;   /* plain searches with no seeds: 0 = the fixed entry vertex (paper,
+                             Sec. 4.4); 1 = per query, the nearest of the index's pivot vertices
+                             (about n/256, at most 4096, chosen at upload) -- not in the paper */
 } deg_search_params;
 
 /* Plain search: one Alg. 1 run per query q of queries_dev [nq][dim] float32, seeded at

@@ -40,7 +40,7 @@ class BuildParams(ctypes.Structure):
 class SearchParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("eps", ctypes.c_float), ("precision", ctypes.c_int32),
                 ("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("visited_cap", ctypes.c_int32),
-                ("queue_cap", ctypes.c_int32)]
+                ("queue_cap", ctypes.c_int32), ("entry_mode", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -186,7 +186,8 @@ class Index:
 
     def search(self, queries=None, k: int = 10, eps: float = 0.1, seeds=None, explore: bool = False,
                precision: str = "f32", rerank: int = 0, max_hops: int = 0, visited_cap: int = 0,
-               queue_cap: int = 0, with_status: bool = False, with_trace: bool = False, out=None, stream=None):
+               queue_cap: int = 0, entry: str = "fixed", with_status: bool = False, with_trace: bool = False,
+               out=None, stream=None):
         """Alg. 1 for a batch of queries (CUDA tensors). Returns (ids, dists[, status][, trace])."""
         import torch
         if explore:
@@ -205,7 +206,8 @@ class Index:
             ids, dists = out
         status = torch.empty(nq, dtype=torch.int32, device=dev) if with_status else None
         trace = torch.empty((nq, 4), dtype=torch.int32, device=dev) if with_trace else None
-        p = SearchParams(k, eps, PRECISIONS[precision], rerank, max_hops, visited_cap, queue_cap)
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, max_hops, visited_cap, queue_cap,
+                         {"fixed": 0, "pivot": 1}[entry])
         _check(lib().deg_search_ex(self._h, ctypes.byref(p), None if explore else _dptr(queries), _dptr(seeds),
                                    1 if explore else 0, nq, _dptr(ids), _dptr(dists), _dptr(status), _dptr(trace),
                                    _stream_ptr(stream)))
@@ -217,12 +219,12 @@ class Index:
         return tuple(res)
 
     def search_host(self, queries: np.ndarray | None, k: int, eps: float, explore_ids: np.ndarray | None = None,
-                    precision: str = "f32", rerank: int = 0, out=None, stream=None):
+                    precision: str = "f32", rerank: int = 0, entry: str = "fixed", out=None, stream=None):
         """End-to-end form: host arrays in and out (pinned numpy views recommended)."""
         explore = explore_ids is not None
         nq = explore_ids.shape[0] if explore else queries.shape[0]
         ids, dists = out if out is not None else (np.empty((nq, k), np.int32), np.empty((nq, k), np.float32))
-        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0)
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry])
         qptr = None if explore else ctypes.c_void_p(queries.ctypes.data)
         sptr = ctypes.c_void_p(explore_ids.ctypes.data) if explore else None
         _check(lib().deg_search_host(self._h, ctypes.byref(p), qptr, sptr, 1 if explore else 0, nq,

@@ -87,6 +87,7 @@ void free_device(deg_index* idx) {
     cudaFree(d.adj);
     cudaFree(d.old2new);
     cudaFree(d.new2old);
+    cudaFree(d.pivots);
     d = DeviceIndex{};
     workspace_free(idx->ws);
     idx->uploaded_mask = 0;
@@ -356,6 +357,8 @@ deg_status validate_search(const deg_index* idx, const deg_search_params* p, con
     if (p->max_hops < 0) return fail(DEG_EINVAL, "search: max_hops must be >= 0");
     if (p->visited_cap != 0) return fail(DEG_EINVAL, "search: visited_cap is reserved and must be 0");
     if (p->queue_cap < 0 || p->queue_cap > 32768) return fail(DEG_EINVAL, "search: queue_cap must be in [0, 32768]");
+    if (p->entry_mode != 0 && p->entry_mode != 1) return fail(DEG_EINVAL, "search: entry_mode must be 0 or 1");
+    if (p->entry_mode == 1 && (explore || seeds)) return fail(DEG_EINVAL, "search: entry_mode 1 needs query vectors and no seeds");
     if (explore ? (queries != nullptr || seeds == nullptr) : (queries == nullptr && nq > 0))
         return fail(DEG_EINVAL, "search: explore needs vertex ids and no query vectors; search needs vectors");
     return DEG_OK;
@@ -373,7 +376,8 @@ extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, 
     std::string why;
     if (workspace_reserve(idx->ws, idx->dev, nq, &why) != 0) return fail(DEG_ENOMEM, "search: workspace: " + why);
     SearchArgs a{&idx->dev, queries_dev, seeds_dev, explore ? 1 : 0, nq, p->k, p->eps, p->precision,
-                 p->rerank, p->max_hops, p->visited_cap, p->queue_cap, ids_dev, dists_dev, status_dev, trace_dev};
+                 p->rerank, p->max_hops, p->visited_cap, p->queue_cap, p->entry_mode, ids_dev, dists_dev,
+                 status_dev, trace_dev};
     const int e = launch_search(a, idx->ws, static_cast<deg_stream_t>(stream), &why);
     if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "search: " + why);
     return DEG_OK;
@@ -382,14 +386,14 @@ extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, 
 extern "C" deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
                                  const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
                                  int32_t* status_dev, void* stream) {
-    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0};
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0};
     return deg_search_ex(idx, &p, queries_dev, seeds_dev, 0, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
 }
 
 extern "C" deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, int64_t nq, int32_t k,
                                   float eps, int32_t* ids_dev, float* dists_dev, int32_t* status_dev,
                                   void* stream) {
-    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0};
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0};
     return deg_search_ex(idx, &p, nullptr, vertex_ids_dev, 1, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
 }
 

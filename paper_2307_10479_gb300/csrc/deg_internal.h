@@ -39,6 +39,8 @@ struct DeviceIndex {
     int32_t* old2new = nullptr;   // [n] caller id -> internal id
     int32_t* new2old = nullptr;   // [n] internal id -> caller id
     int32_t entry_internal = -1;
+    int32_t* pivots = nullptr;    // [npivots] internal ids of the layout's pivots
+    int32_t npivots = 0;
 };
 
 // Scratch of the search kernels: the overflow list, and per-warp device-memory state (a visited
@@ -47,6 +49,7 @@ struct DeviceIndex {
 struct Workspace {
     int32_t* counters = nullptr;     // [0] overflow count, [1] second-kernel cursor, [2] main cursor
     int32_t* overflow = nullptr;     // [cap_q] query indices
+    int32_t* route = nullptr;        // [2 * cap_q] pivot labels and routed seeds (internal ids)
     int64_t cap_q = 0;
     int64_t words = 0;               // 32-bit words of one visited bitmap
     uint32_t* bitmaps = nullptr;     // main kernel: [slots][words]
@@ -75,6 +78,7 @@ struct SearchArgs {
     int32_t max_hops;
     int32_t visited_cap;
     int32_t queue_cap;
+    int32_t entry_mode;
     int32_t* ids;
     float* dists;
     int32_t* status;
@@ -91,6 +95,10 @@ int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why)
 
 // Reorder rows and adjacency by nearest pivot (layout.cu); fills old2new/new2old. Synchronous.
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+
+// Entry routing (layout.cu): seeds[q] = internal id of the pivot nearest to query q.
+int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
+                    deg_stream_t stream, std::string* why);
 
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);

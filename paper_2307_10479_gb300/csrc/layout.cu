@@ -20,8 +20,10 @@ namespace {
 
 constexpr int kTile = 64, kKc = 32, kChunk = 1024;
 
-// labels[v] = argmin_p |x_v - x_{pivot p}|^2 (ties -> lower p). 64 rows x 64 pivots per tile.
-__global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restrict__ x, int64_t n, int32_t dim,
+// labels[v] = argmin_p |r_v - x_{pivot p}|^2 (ties -> lower p) for rows r_v = rows[v * rstride..]
+// and pivot rows x[pivots[p] * dim_pad..]. 64 rows x 64 pivots per tile.
+__global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restrict__ rows, int64_t rstride,
+                                                            const float* __restrict__ x, int64_t n, int32_t dim,
                                                             int32_t dim_pad, const int32_t* __restrict__ pivots,
                                                             int32_t np, int32_t* __restrict__ labels) {
     __shared__ float xs[kKc][kTile + 4];
@@ -35,7 +37,7 @@ __global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restr
             for (int t = threadIdx.x; t < kTile * kKc; t += 256) {
                 const int r = t / kKc, c = t % kKc;
                 const bool kc = k0 + c < dim;
-                xs[c][r] = (kc && r0 + r < n) ? x[(r0 + r) * dim_pad + k0 + c] : 0.f;
+                xs[c][r] = (kc && r0 + r < n) ? rows[(r0 + r) * rstride + k0 + c] : 0.f;
                 ps[c][r] = (kc && p0 + r < np) ? x[(int64_t)pivots[p0 + r] * dim_pad + k0 + c] : 0.f;
             }
             __syncthreads();
@@ -156,6 +158,11 @@ __global__ void pivot_ids_kernel(int32_t* pivots, int32_t np, int64_t stride) {
     if (p < np) pivots[p] = (int32_t)(p * stride);
 }
 
+__global__ void map_ids_kernel(const int32_t* in, int32_t count, const int32_t* table, int32_t* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) out[i] = table[in[i]];
+}
+
 }  // namespace
 
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why) {
@@ -181,7 +188,8 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
         return *why = std::string("layout buffers: ") + cudaGetErrorString(e), (int)e;
     }
     pivot_ids_kernel<<<(np + 255) / 256, 256, 0, st>>>(pivots, np, n / np);
-    nearest_pivot_kernel<<<(unsigned)((n + kTile - 1) / kTile), 256, 0, st>>>(ix.x32, n, ix.dim, ix.dim_pad, pivots, np, labels);
+    nearest_pivot_kernel<<<(unsigned)((n + kTile - 1) / kTile), 256, 0, st>>>(ix.x32, ix.dim_pad, ix.x32, n, ix.dim,
+                                                                              ix.dim_pad, pivots, np, labels);
     chunk_hist_kernel<<<(unsigned)nchunks, 256, 4 * np, st>>>(labels, n, np, chunk_hist);
     label_scan_kernel<<<(np + 127) / 128, 128, 0, st>>>(chunk_hist, nchunks, np, totals);
     offsets_kernel<<<1, 32, 0, st>>>(totals, np, offsets);
@@ -196,6 +204,13 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     }
     std::swap(ix.x32, x2);
     std::swap(ix.adj, adj2);
+    // keep the pivots, as internal ids, for routing queries to an entry vertex
+    if ((e = cudaMalloc(&ix.pivots, 4 * np)) != cudaSuccess) {
+        cleanup();
+        return *why = cudaGetErrorString(e), (int)e;
+    }
+    map_ids_kernel<<<(np + 255) / 256, 256, 0, st>>>(pivots, np, ix.old2new, ix.pivots);
+    ix.npivots = np;
     int32_t entry_new = -1;
     if ((e = cudaMemcpy(&entry_new, ix.old2new + ix.entry, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
         cleanup();
@@ -203,6 +218,21 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     }
     ix.entry_internal = entry_new;
     cleanup();  // frees the old rows and adjacency (swapped into x2 / adj2) and the scratch
+    return 0;
+}
+
+}  // namespace deg
+
+namespace deg {
+
+int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
+                    deg_stream_t stream, std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    nearest_pivot_kernel<<<(unsigned)((nq + kTile - 1) / kTile), 256, 0, st>>>(queries, ix.dim, ix.x32, nq, ix.dim,
+                                                                               ix.dim_pad, ix.pivots, ix.npivots, labels);
+    map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;
 }
 

@@ -139,6 +139,7 @@ struct Params {
     const float* queries;
     int32_t dim;
     const int32_t* seeds;
+    int32_t seeds_internal;    // 1: seeds are internal ids already (pivot routing)
     int32_t explore;
     int32_t nq;
     int32_t k;                 // results returned
@@ -499,7 +500,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     const bool given = P.explore || P.seeds;
     const int32_t seed_in = given ? P.seeds[q] : 0;
     const bool seed_ok = !given || (seed_in >= 0 && seed_in < P.n);
-    const int32_t seed = !given ? P.entry : (seed_ok ? __ldg(P.old2new + seed_in) : 0);
+    const int32_t seed = !given ? P.entry : (!seed_ok ? 0 : P.seeds_internal ? seed_in : __ldg(P.old2new + seed_in));
     const float* qsrc = P.explore ? P.x32 + (int64_t)(seed_ok ? seed : 0) * P.dim_pad : P.queries + (int64_t)q * P.dim;
     const int dim4 = (P.dim + 3) / 4 * 4;
     for (int i = lane; i < dim4; i += 32) qv_smem[i] = i < P.dim ? qsrc[i] : 0.f;
@@ -725,7 +726,11 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         cudaFree(ws.overflow);
         ws.overflow = nullptr;
         ws.cap_q = 0;
-        if ((e = cudaMalloc(&ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess) return *why = "overflow list", (int)e;
+        cudaFree(ws.route);
+        ws.route = nullptr;
+        if ((e = cudaMalloc(&ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.route, 2 * sizeof(int32_t) * nq)) != cudaSuccess)
+            return *why = "overflow list", (int)e;
         ws.cap_q = nq;
     }
     if (!ws.bitmaps) {
@@ -759,6 +764,7 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
 void workspace_free(Workspace& ws) {
     cudaFree(ws.counters);
     cudaFree(ws.overflow);
+    cudaFree(ws.route);
     cudaFree(ws.bitmaps);
     cudaFree(ws.backs);
     cudaFree(ws.pbitmaps);
@@ -787,6 +793,13 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.dim = ix.dim;
     P.seeds = a.seeds;
     P.explore = a.explore;
+    if (a.entry_mode == 1 && !a.explore && !a.seeds) {
+        // route every query to its nearest pivot first; those become internal seeds
+        const int e = route_to_pivots(ix, a.queries, a.nq, ws.route, ws.route + ws.cap_q, stream, why);
+        if (e != 0) return e;
+        P.seeds = ws.route + ws.cap_q;
+        P.seeds_internal = 1;
+    }
     P.nq = (int32_t)a.nq;
     P.k = a.k;
     const bool reduced = a.precision != DEG_F32;

@@ -149,3 +149,19 @@ def test_stream_ordering_on_a_side_stream(cfg1):
         ids, _ = idx.search(cfg1["qd"], k=10, eps=0.1)
     s.synchronize()
     assert torch.equal(ids, ref_ids)
+
+
+def test_pivot_entry_parity(cfg1):
+    # entry="pivot": each query starts at the nearest of the pivots p * (n // P), P = n // 256
+    # (at most 4096). The oracle picks that pivot by FP64 brute force and runs Alg. 1 from it.
+    idx, q, base, adj = cfg1["idx"], cfg1["q"], cfg1["base"], cfg1["adj"]
+    n = len(base)
+    npv = max(1, min(4096, n // 256))
+    piv = (np.arange(npv) * (n // npv)).astype(np.int32)
+    lab, _ = oracle.knn_bruteforce(base[piv], q, 1)
+    seeds = piv[lab[:, 0]]
+    ids, d = idx.search(cfg1["qd"], k=10, eps=0.1, entry="pivot")
+    o_ids, o_d, _ = oracle.range_search(base, adj, q, seeds, 10, 0.1)
+    compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d)
+    with pytest.raises(cfg1["deg"].DegError):
+        idx.search(cfg1["qd"], k=10, eps=0.1, entry="pivot", seeds=torch.zeros(len(q), dtype=torch.int32, device="cuda"))

@@ -31,7 +31,7 @@ from paper_2307_10479_gb300 import synth  # noqa: E402
 WORKLOAD = "sift-1m-d128"
 K = 10
 TARGET_RECALL = 0.95
-EPS_GRID = [round(0.02 * i, 2) for i in range(0, 21)]
+EPS_GRID = [round(0.005 * i, 3) for i in range(0, 21)] + [round(0.12 + 0.02 * i, 2) for i in range(0, 15)]
 METRIC = "QPS at recall@10>=0.95 (1M x 128), vs plain FP32 search; p50/p99 ms; HBM GB/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "search_traffic.txt")
@@ -328,6 +328,20 @@ def main():
     forms["plain float32, fixed entry"] = plain
     for name in list(FORMS)[1:]:
         forms[name], _ = measure(name, FORMS[name], max(3, args.steps // 4), args.warmup)
+    # learned early stop: trained (untimed) with the library's kernels on traces of 50,000 held-out
+    # queries of the fp8 / pivot-entry form, then measured like the other forms
+    base_name = "fp8 + re-rank 32, pivot entry"
+    t_eps = forms[base_name]["eps"] + 0.01
+    tq = torch.from_numpy(w.training_queries(50000)).cuda()
+    feats, labels, counts = idx.stop_record(tq, k=K, eps=t_eps, cap=512, **FORMS[base_name])
+    mask = torch.arange(512, device="cuda")[None, :] < counts[:, None]
+    wts, hist = deg.train_stop_model(feats[mask].contiguous(), labels[mask].contiguous(), epochs=4, batch=8192)
+    log(f"[bench] stop model: {int(mask.sum())} samples, loss {[round(h, 4) for h in hist]}")
+    del feats, labels, counts, mask, tq
+    idx.set_stop_model(wts, 0.7)
+    lname = base_name + ", learned stop (P>0.7)"
+    FORMS[lname] = dict(FORMS[base_name], learned_stop=True)
+    forms[lname], _ = measure(lname, FORMS[lname], max(3, args.steps // 4), args.warmup)
     ok = {k: v for k, v in forms.items() if v["recall_at_10"] >= TARGET_RECALL}
     best = max(ok or forms, key=lambda k: (ok or forms)[k]["qps"])
     # the headline: the fastest form, timed again over the full step count with clocks sampled

@@ -133,6 +133,9 @@ typedef struct {
     int32_t entry_mode;   /* plain searches with no seeds: 0 = the fixed entry vertex (paper,
                              Sec. 4.4); 1 = per query, the nearest of the index's pivot vertices
                              (about n/256, at most 4096, chosen at upload) -- not in the paper */
+    int32_t learned_stop; /* 1: after every hop the index's stop network (deg_set_stop_model)
+                             may end the search early; the eps test still applies. Not in the
+                             paper; 0 = the plain method */
 } deg_search_params;
 
 /* Plain search: one Alg. 1 run per query q of queries_dev [nq][dim] float32, seeded at
@@ -166,6 +169,42 @@ DEG_API deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, con
 DEG_API deg_status deg_search_host(deg_index* idx, const deg_search_params* p, const float* queries_host,
                            const int32_t* seeds_host, int32_t explore, int64_t nq,
                            int32_t* ids_host, float* dists_host, void* stream);
+
+/* ---- learned early stop (library extension; the paper stops by the eps test alone) --------
+ * A 12-64-64-2 perceptron (ReLU; 5,122 float32 parameters laid out W1 [64][12], b1 [64],
+ * W2 [64][64], b2 [64], W3 [2][64], b3 [2]; logit 1 = stop) reads 12 features of the search state
+ * after each hop and predicts whether the result list is already final. */
+
+#define DEG_STOP_FEATURES 12
+#define DEG_STOP_PARAMS 5122
+
+/* Training traces: run the plain search (p->learned_stop ignored) and record, for each of the
+ * first `cap` hops of query q, the 12 features (feats_dev [nq][cap][12] float32) and the label
+ * 1 if the result list never changed after that hop, else 0 (labels_dev [nq][cap] int32);
+ * counts_dev [nq] int32 gets the number of hops recorded. Slots past the count are untouched. */
+DEG_API deg_status deg_stop_record(deg_index* idx, const deg_search_params* p, const float* queries_dev,
+                                   int64_t nq, int32_t cap, float* feats_dev, int32_t* labels_dev,
+                                   int32_t* counts_dev, void* stream);
+
+/* Mean softmax cross-entropy of `count` samples x_dev [count][12] with labels_dev [count] and its
+ * gradient grad_dev [5122] (loss_dev [1], nullable). scratch_dev holds
+ * deg_mlp_scratch_floats(count) floats. Deterministic (fixed summation order). */
+DEG_API deg_status deg_mlp_loss_grad(const float* w_dev, const float* x_dev, const int32_t* labels_dev, int64_t count,
+                                     float* grad_dev, float* loss_dev, float* scratch_dev, void* stream);
+DEG_API int64_t deg_mlp_scratch_floats(int64_t count);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) of w_dev with moments m_dev, v_dev (all [5122]);
+ * step counts from 1. */
+DEG_API deg_status deg_mlp_adam(float* w_dev, float* m_dev, float* v_dev, const float* grad_dev, int32_t step,
+                                float lr, void* stream);
+
+/* p_stop_dev [count] = softmax(network(x))[stop]. */
+DEG_API deg_status deg_mlp_predict(const float* w_dev, const float* x_dev, int64_t count, float* p_stop_dev,
+                                   void* stream);
+
+/* Install a trained network on an uploaded index (stored in bfloat16 for the search) with the
+ * decision threshold: stop when P(stop) > threshold, 0 < threshold < 1. */
+DEG_API deg_status deg_set_stop_model(deg_index* idx, const float* w_dev, float threshold, void* stream);
 
 /* ---- exact ground truth (Eq. 1) ----------------------------------------------------------- */
 

@@ -15,7 +15,7 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRCS = ["oracle_search.cpp", "oracle_build.cpp", "oracle_quant.cpp"]
+_SRCS = ["oracle_search.cpp", "oracle_build.cpp", "oracle_quant.cpp", "oracle_mlp.cpp"]
 _LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -65,6 +65,10 @@ def lib() -> ctypes.CDLL:
             L.oracle_decode.argtypes = [i32, P, P, i64, i32, P]
             L.oracle_range_search_decoded.argtypes = [P, P, i64, i32, P, i32, P, P, i64, i32, i32, i32, f64, P, P, i32]
             L.oracle_range_search_decoded.restype = ctypes.c_int
+            L.oracle_mlp_nparams.restype = ctypes.c_int
+            L.oracle_mlp_loss_grad.argtypes = [P, P, P, i64, P]
+            L.oracle_mlp_loss_grad.restype = f64
+            L.oracle_mlp_predict.argtypes = [P, P, i64, P]
             _lib = L
     return _lib
 
@@ -213,3 +217,28 @@ def range_search_decoded(decoded, base, adj, queries, seeds, k, eps, keep=None, 
     if rc:
         raise ValueError("oracle_range_search_decoded: invalid arguments")
     return ids, dists
+
+
+MLP_SHAPES = [("W1", (64, 12)), ("b1", (64,)), ("W2", (64, 64)), ("b2", (64,)), ("W3", (2, 64)), ("b3", (2,))]
+
+
+def mlp_nparams() -> int:
+    return int(lib().oracle_mlp_nparams())
+
+
+def mlp_loss_grad(w, x, labels, with_grad=True):
+    """Learned-stop network in FP64: mean softmax cross-entropy and its gradient (flat 5122)."""
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float32)
+    labels = np.ascontiguousarray(labels, np.int32)
+    g = np.empty(mlp_nparams(), np.float64) if with_grad else None
+    loss = lib().oracle_mlp_loss_grad(_ptr(w), _ptr(x), _ptr(labels), x.shape[0], _ptr(g))
+    return (loss, g) if with_grad else loss
+
+
+def mlp_predict(w, x):
+    w = np.ascontiguousarray(w, np.float64)
+    x = np.ascontiguousarray(x, np.float32)
+    p = np.empty(x.shape[0], np.float64)
+    lib().oracle_mlp_predict(_ptr(w), _ptr(x), x.shape[0], _ptr(p))
+    return p

@@ -40,7 +40,7 @@ class BuildParams(ctypes.Structure):
 class SearchParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("eps", ctypes.c_float), ("precision", ctypes.c_int32),
                 ("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("visited_cap", ctypes.c_int32),
-                ("queue_cap", ctypes.c_int32), ("entry_mode", ctypes.c_int32)]
+                ("queue_cap", ctypes.c_int32), ("entry_mode", ctypes.c_int32), ("learned_stop", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -75,6 +75,12 @@ def lib() -> ctypes.CDLL:
             "deg_search_host": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P]),
             "knn_exact": (S, [P, i64, P, i64, i32, i32, P, P, P]),
             "knn_exact_noalloc": (S, [P, i64, P, i64, i32, i32, P, P, P]),
+            "deg_stop_record": (S, [P, ctypes.POINTER(SearchParams), P, i64, i32, P, P, P, P]),
+            "deg_mlp_loss_grad": (S, [P, P, P, i64, P, P, P, P]),
+            "deg_mlp_scratch_floats": (i64, [i64]),
+            "deg_mlp_adam": (S, [P, P, P, P, i32, f32, P]),
+            "deg_mlp_predict": (S, [P, P, i64, P, P]),
+            "deg_set_stop_model": (S, [P, P, f32, P]),
             "deg_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -186,8 +192,8 @@ class Index:
 
     def search(self, queries=None, k: int = 10, eps: float = 0.1, seeds=None, explore: bool = False,
                precision: str = "f32", rerank: int = 0, max_hops: int = 0, visited_cap: int = 0,
-               queue_cap: int = 0, entry: str = "fixed", with_status: bool = False, with_trace: bool = False,
-               out=None, stream=None):
+               queue_cap: int = 0, entry: str = "fixed", learned_stop: bool = False, with_status: bool = False,
+               with_trace: bool = False, out=None, stream=None):
         """Alg. 1 for a batch of queries (CUDA tensors). Returns (ids, dists[, status][, trace])."""
         import torch
         if explore:
@@ -207,7 +213,7 @@ class Index:
         status = torch.empty(nq, dtype=torch.int32, device=dev) if with_status else None
         trace = torch.empty((nq, 4), dtype=torch.int32, device=dev) if with_trace else None
         p = SearchParams(k, eps, PRECISIONS[precision], rerank, max_hops, visited_cap, queue_cap,
-                         {"fixed": 0, "pivot": 1}[entry])
+                         {"fixed": 0, "pivot": 1}[entry], 1 if learned_stop else 0)
         _check(lib().deg_search_ex(self._h, ctypes.byref(p), None if explore else _dptr(queries), _dptr(seeds),
                                    1 if explore else 0, nq, _dptr(ids), _dptr(dists), _dptr(status), _dptr(trace),
                                    _stream_ptr(stream)))
@@ -219,18 +225,109 @@ class Index:
         return tuple(res)
 
     def search_host(self, queries: np.ndarray | None, k: int, eps: float, explore_ids: np.ndarray | None = None,
-                    precision: str = "f32", rerank: int = 0, entry: str = "fixed", out=None, stream=None):
+                    precision: str = "f32", rerank: int = 0, entry: str = "fixed", learned_stop: bool = False,
+                    out=None, stream=None):
         """End-to-end form: host arrays in and out (pinned numpy views recommended)."""
         explore = explore_ids is not None
         nq = explore_ids.shape[0] if explore else queries.shape[0]
         ids, dists = out if out is not None else (np.empty((nq, k), np.int32), np.empty((nq, k), np.float32))
-        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry])
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry],
+                         1 if learned_stop else 0)
         qptr = None if explore else ctypes.c_void_p(queries.ctypes.data)
         sptr = ctypes.c_void_p(explore_ids.ctypes.data) if explore else None
         _check(lib().deg_search_host(self._h, ctypes.byref(p), qptr, sptr, 1 if explore else 0, nq,
                                      ctypes.c_void_p(ids.ctypes.data), ctypes.c_void_p(dists.ctypes.data),
                                      _stream_ptr(stream)))
         return ids, dists
+
+
+    # ---- learned early stop -----------------------------------------------------------------
+    def stop_record(self, queries, k: int, eps: float, cap: int = 256, precision: str = "f32", rerank: int = 0,
+                    entry: str = "fixed", stream=None):
+        """Training traces of the plain search: (features [nq, cap, 12], labels [nq, cap], counts [nq])."""
+        import torch
+        queries = _require_cuda(queries, torch.float32, "queries")
+        nq = queries.shape[0]
+        feats = torch.zeros((nq, cap, STOP_FEATURES), dtype=torch.float32, device=queries.device)
+        labels = torch.zeros((nq, cap), dtype=torch.int32, device=queries.device)
+        counts = torch.zeros(nq, dtype=torch.int32, device=queries.device)
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry], 0)
+        _check(lib().deg_stop_record(self._h, ctypes.byref(p), _dptr(queries), nq, cap, _dptr(feats), _dptr(labels),
+                                     _dptr(counts), _stream_ptr(stream)))
+        return feats, labels, counts
+
+    def set_stop_model(self, weights, threshold: float, stream=None):
+        import torch
+        weights = _require_cuda(weights, torch.float32, "weights")
+        _check(lib().deg_set_stop_model(self._h, _dptr(weights), float(threshold), _stream_ptr(stream)))
+
+
+STOP_FEATURES, STOP_PARAMS = 12, 5122
+
+
+def mlp_loss_grad(w, x, labels, stream=None):
+    """Mean loss and gradient of the stop network on the device (the library's kernels)."""
+    import torch
+    w = _require_cuda(w, torch.float32, "weights")
+    x = _require_cuda(x, torch.float32, "features")
+    labels = _require_cuda(labels, torch.int32, "labels")
+    count = x.shape[0]
+    grad = torch.empty(STOP_PARAMS, dtype=torch.float32, device=w.device)
+    loss = torch.empty(1, dtype=torch.float32, device=w.device)
+    scratch = torch.empty(int(lib().deg_mlp_scratch_floats(count)), dtype=torch.float32, device=w.device)
+    _check(lib().deg_mlp_loss_grad(_dptr(w), _dptr(x), _dptr(labels), count, _dptr(grad), _dptr(loss), _dptr(scratch),
+                                   _stream_ptr(stream)))
+    return loss, grad
+
+
+def mlp_adam(w, m, v, grad, step: int, lr: float, stream=None):
+    _check(lib().deg_mlp_adam(_dptr(w), _dptr(m), _dptr(v), _dptr(grad), step, float(lr), _stream_ptr(stream)))
+
+
+def mlp_predict(w, x, stream=None):
+    import torch
+    p = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().deg_mlp_predict(_dptr(w), _dptr(x), x.shape[0], _dptr(p), _stream_ptr(stream)))
+    return p
+
+
+def mlp_init(seed: int = 0):
+    """He-uniform initial weights (host numpy, float32), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_in, fan_out in ((12, 64), (64, 64), (64, 2)):
+        lim = np.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, (fan_out, fan_in)).ravel())
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def train_stop_model(feats, labels, epochs: int = 4, batch: int = 8192, lr: float = 2e-3, seed: int = 0,
+                     pos_weight_balance: bool = False, log=None):
+    """Train the stop network with the library's kernels: minibatch Adam on (features, labels)
+    CUDA tensors. Returns the float32 weights (CUDA tensor) and the per-epoch mean loss."""
+    import torch
+    w = torch.from_numpy(mlp_init(seed)).cuda()
+    m = torch.zeros_like(w)
+    v = torch.zeros_like(w)
+    n = feats.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    step, hist = 0, []
+    for ep in range(epochs):
+        perm = torch.randperm(n, generator=g).cuda()
+        tot = 0.0
+        for b0 in range(0, n, batch):
+            sel = perm[b0:b0 + batch]
+            x = feats[sel].contiguous()
+            y = labels[sel].contiguous()
+            loss, grad = mlp_loss_grad(w, x, y)
+            step += 1
+            mlp_adam(w, m, v, grad, step, lr)
+            tot += float(loss.item()) * len(sel)
+        hist.append(tot / n)
+        if log:
+            log(f"stop model epoch {ep}: loss {hist[-1]:.4f}")
+    return w, hist
 
 
 def knn_exact(base, queries, k: int, stream=None):

@@ -88,6 +88,7 @@ void free_device(deg_index* idx) {
     cudaFree(d.old2new);
     cudaFree(d.new2old);
     cudaFree(d.pivots);
+    cudaFree(d.stop_w);
     d = DeviceIndex{};
     workspace_free(idx->ws);
     idx->uploaded_mask = 0;
@@ -358,6 +359,7 @@ deg_status validate_search(const deg_index* idx, const deg_search_params* p, con
     if (p->visited_cap != 0) return fail(DEG_EINVAL, "search: visited_cap is reserved and must be 0");
     if (p->queue_cap < 0 || p->queue_cap > 32768) return fail(DEG_EINVAL, "search: queue_cap must be in [0, 32768]");
     if (p->entry_mode != 0 && p->entry_mode != 1) return fail(DEG_EINVAL, "search: entry_mode must be 0 or 1");
+    if (p->learned_stop != 0 && p->learned_stop != 1) return fail(DEG_EINVAL, "search: learned_stop must be 0 or 1");
     if (p->entry_mode == 1 && (explore || seeds)) return fail(DEG_EINVAL, "search: entry_mode 1 needs query vectors and no seeds");
     if (explore ? (queries != nullptr || seeds == nullptr) : (queries == nullptr && nq > 0))
         return fail(DEG_EINVAL, "search: explore needs vertex ids and no query vectors; search needs vectors");
@@ -375,9 +377,10 @@ extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, 
     if (!ids_dev || !dists_dev) return fail(DEG_EINVAL, "search: NULL output");
     std::string why;
     if (workspace_reserve(idx->ws, idx->dev, nq, &why) != 0) return fail(DEG_ENOMEM, "search: workspace: " + why);
+    if (p->learned_stop && !idx->dev.stop_w) return fail(DEG_ENOTREADY, "search: no stop model (deg_set_stop_model)");
     SearchArgs a{&idx->dev, queries_dev, seeds_dev, explore ? 1 : 0, nq, p->k, p->eps, p->precision,
-                 p->rerank, p->max_hops, p->visited_cap, p->queue_cap, p->entry_mode, ids_dev, dists_dev,
-                 status_dev, trace_dev};
+                 p->rerank, p->max_hops, p->visited_cap, p->queue_cap, p->entry_mode, p->learned_stop ? 1 : 0,
+                 nullptr, nullptr, nullptr, 0, ids_dev, dists_dev, status_dev, trace_dev};
     const int e = launch_search(a, idx->ws, static_cast<deg_stream_t>(stream), &why);
     if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "search: " + why);
     return DEG_OK;
@@ -386,14 +389,14 @@ extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, 
 extern "C" deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
                                  const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
                                  int32_t* status_dev, void* stream) {
-    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0};
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0, 0};
     return deg_search_ex(idx, &p, queries_dev, seeds_dev, 0, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
 }
 
 extern "C" deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, int64_t nq, int32_t k,
                                   float eps, int32_t* ids_dev, float* dists_dev, int32_t* status_dev,
                                   void* stream) {
-    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0};
+    deg_search_params p{k, eps, DEG_F32, 0, 0, 0, 0, 0, 0};
     return deg_search_ex(idx, &p, nullptr, vertex_ids_dev, 1, nq, ids_dev, dists_dev, status_dev, nullptr, stream);
 }
 
@@ -465,5 +468,84 @@ extern "C" deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const 
     const int e = launch_knn_exact_noalloc(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
                                            static_cast<deg_stream_t>(stream), &why);
     if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "knn_exact_noalloc: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_stop_record(deg_index* idx, const deg_search_params* p, const float* queries_dev,
+                                      int64_t nq, int32_t cap, float* feats_dev, int32_t* labels_dev,
+                                      int32_t* counts_dev, void* stream) {
+    deg_status s = validate_search(idx, p, queries_dev, nullptr, 0, nq);
+    if (s != DEG_OK) return s;
+    if (cap < 1) return fail(DEG_EINVAL, "stop_record: cap must be >= 1");
+    if (nq == 0) return DEG_OK;
+    if (!feats_dev || !labels_dev || !counts_dev) return fail(DEG_EINVAL, "stop_record: NULL output");
+    std::string why;
+    if (workspace_reserve(idx->ws, idx->dev, nq, &why) != 0) return fail(DEG_ENOMEM, "stop_record: workspace: " + why);
+    // results of the recording run are not needed: reuse the e2e staging buffers
+    Workspace& ws = idx->ws;
+    if (ws.stage_q < nq || ws.stage_k < p->k) {
+        cudaFree(ws.dq); cudaFree(ws.did); cudaFree(ws.dd);
+        ws.dq = ws.did = ws.dd = nullptr;
+        ws.stage_q = ws.stage_k = 0;
+        cudaError_t e;
+        const size_t qb = std::max<size_t>(sizeof(float) * (size_t)nq * idx->dim, sizeof(int32_t) * (size_t)nq);
+        if ((e = cudaMalloc(&ws.dq, qb)) != cudaSuccess || (e = cudaMalloc(&ws.did, sizeof(int32_t) * nq * p->k)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.dd, sizeof(float) * nq * p->k)) != cudaSuccess)
+            return fail(DEG_ENOMEM, std::string("stop_record: cudaMalloc: ") + cudaGetErrorString(e));
+        ws.stage_q = nq;
+        ws.stage_k = p->k;
+    }
+    SearchArgs a{&idx->dev, queries_dev, nullptr, 0, nq, p->k, p->eps, p->precision, p->rerank, p->max_hops,
+                 p->visited_cap, p->queue_cap, p->entry_mode, 0, feats_dev, labels_dev, counts_dev, cap,
+                 static_cast<int32_t*>(ws.did), static_cast<float*>(ws.dd), nullptr, nullptr};
+    const int e = launch_search(a, idx->ws, static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) return fail(DEG_ECUDA, "stop_record: " + why);
+    return DEG_OK;
+}
+
+extern "C" int64_t deg_mlp_scratch_floats(int64_t count) { return count > 0 ? mlp_scratch_floats(count) : 0; }
+
+extern "C" deg_status deg_mlp_loss_grad(const float* w_dev, const float* x_dev, const int32_t* labels_dev, int64_t count,
+                                        float* grad_dev, float* loss_dev, float* scratch_dev, void* stream) {
+    if (!w_dev || !x_dev || !labels_dev || !grad_dev || !scratch_dev || count < 1)
+        return fail(DEG_EINVAL, "mlp_loss_grad: bad arguments");
+    std::string why;
+    if (mlp_loss_grad(w_dev, x_dev, labels_dev, count, grad_dev, loss_dev, scratch_dev,
+                      static_cast<deg_stream_t>(stream), &why) != 0)
+        return fail(DEG_ECUDA, "mlp_loss_grad: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_mlp_adam(float* w_dev, float* m_dev, float* v_dev, const float* grad_dev, int32_t step,
+                                   float lr, void* stream) {
+    if (!w_dev || !m_dev || !v_dev || !grad_dev || step < 1 || !(lr > 0.f)) return fail(DEG_EINVAL, "mlp_adam: bad arguments");
+    std::string why;
+    if (mlp_adam(w_dev, m_dev, v_dev, grad_dev, step, lr, static_cast<deg_stream_t>(stream), &why) != 0)
+        return fail(DEG_ECUDA, "mlp_adam: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_mlp_predict(const float* w_dev, const float* x_dev, int64_t count, float* p_stop_dev,
+                                      void* stream) {
+    if (count == 0) return DEG_OK;
+    if (!w_dev || !x_dev || !p_stop_dev || count < 0) return fail(DEG_EINVAL, "mlp_predict: bad arguments");
+    std::string why;
+    if (mlp_predict(w_dev, x_dev, count, p_stop_dev, static_cast<deg_stream_t>(stream), &why) != 0)
+        return fail(DEG_ECUDA, "mlp_predict: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_set_stop_model(deg_index* idx, const float* w_dev, float threshold, void* stream) {
+    if (!idx || !w_dev) return fail(DEG_EINVAL, "set_stop_model: NULL argument");
+    if (!(threshold > 0.f && threshold < 1.f)) return fail(DEG_EINVAL, "set_stop_model: threshold must be in (0, 1)");
+    if (!idx->dev.x32) return fail(DEG_ENOTREADY, "set_stop_model: index not uploaded");
+    cudaError_t e;
+    if (!idx->dev.stop_w && (e = cudaMalloc(&idx->dev.stop_w, 2 * kStopParams)) != cudaSuccess)
+        return cuda_fail(e, "set_stop_model");
+    std::string why;
+    if (mlp_pack_inference(w_dev, idx->dev.stop_w, static_cast<deg_stream_t>(stream), &why) != 0)
+        return fail(DEG_ECUDA, "set_stop_model: " + why);
+    idx->dev.stop_logit = std::log(threshold / (1.f - threshold));
+    if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess) return cuda_fail(e, "set_stop_model");
     return DEG_OK;
 }

@@ -13,6 +13,9 @@ typedef CUstream_st* deg_stream_t;
 
 namespace deg {
 
+constexpr int kStopFeatures = 12;   // inputs of the learned-stop network
+constexpr int kStopParams = 5122;   // 12*64 + 64 + 64*64 + 64 + 2*64 + 2
+
 // Host-side graph construction (builder.cpp).
 int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& p, int32_t* adj_out,
                 volatile int64_t* progress);
@@ -41,6 +44,8 @@ struct DeviceIndex {
     int32_t entry_internal = -1;
     int32_t* pivots = nullptr;    // [npivots] internal ids of the layout's pivots
     int32_t npivots = 0;
+    uint16_t* stop_w = nullptr;   // learned-stop weights, bfloat16, inference layout (mlp.cu)
+    float stop_logit = 0.f;       // stop when logit(stop) - logit(continue) > this
 };
 
 // Scratch of the search kernels: the overflow list, and per-warp device-memory state (a visited
@@ -79,6 +84,11 @@ struct SearchArgs {
     int32_t visited_cap;
     int32_t queue_cap;
     int32_t entry_mode;
+    int32_t learned_stop;
+    float* rec_feats;         // training traces: [nq][rec_cap][kStopFeatures] (or null)
+    int32_t* rec_labels;      //   [nq][rec_cap]
+    int32_t* rec_counts;      //   [nq]
+    int32_t rec_cap;
     int32_t* ids;
     float* dists;
     int32_t* status;
@@ -103,6 +113,14 @@ int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 int make_fp8_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);
+
+// Learned-stop network (mlp.cu).
+int mlp_loss_grad(const float* w, const float* x, const int32_t* labels, int64_t count, float* grad, float* loss,
+                  float* scratch, deg_stream_t stream, std::string* why);
+int64_t mlp_scratch_floats(int64_t count);
+int mlp_adam(float* w, float* m, float* v, const float* g, int step, float lr, deg_stream_t stream, std::string* why);
+int mlp_predict(const float* w, const float* x, int64_t count, float* p_stop, deg_stream_t stream, std::string* why);
+int mlp_pack_inference(const float* w, uint16_t* out, deg_stream_t stream, std::string* why);
 
 // Exact kNN (knn_exact.cu).
 int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,

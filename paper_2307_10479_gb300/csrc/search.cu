@@ -149,6 +149,14 @@ struct Params {
     float f;                   // (1 + eps)^2
     int32_t max_hops;
     int32_t wpb;               // warps per block
+    // learned early stop (not in the paper): network weights, decision margin, trace recording
+    const __nv_bfloat16* stop_w;   // inference layout (mlp.cu), or null
+    float stop_logit;
+    int32_t learned;           // 1: stop when the network's margin exceeds stop_logit
+    float* rec_feats;          // training traces: [nq][rec_cap][kStopFeatures], or null
+    int32_t* rec_labels;
+    int32_t* rec_counts;
+    int32_t rec_cap;
     // outputs
     int32_t* ids;
     float* dists;
@@ -180,6 +188,9 @@ struct WarpState {
     bool trimmed;
     float r2;
     int32_t hops, evals, peak;
+    // for the learned stop's features
+    int32_t last_change, evals_change, hop_rins;
+    float r2_first;
 };
 
 template <class Rows, int G, int CPL>
@@ -287,10 +298,80 @@ __device__ __forceinline__ void result_insert(WarpState& W, int ks, uint64_t c, 
         if (!full) ++W.res_n;
         __syncwarp();
     }
+    if (!full || pos < ks) {
+        W.last_change = W.hops;
+        W.evals_change = W.evals;
+        ++W.hop_rins;
+    }
     if (full) {
+        if (!W.trimmed) W.r2_first = key_d2(W.res[ks - 1]);
         W.trimmed = true;
         W.r2 = key_d2(W.res[ks - 1]);
     }
+}
+
+// ---- learned early stop -------------------------------------------------------------------
+// Twelve warp-uniform features of the search state after a hop (the same code makes the
+// training traces and feeds the network during a search).
+__device__ __forceinline__ float stop_feature(const WarpState& W, int i, float d2_pop, int cnt, int adm, float f) {
+    const float inf = __int_as_float(0x7f800000);
+    switch (i) {
+        case 0: return W.hops * (1.f / 64.f);
+        case 1: return W.evals * (1.f / 1024.f);
+        case 2: return log2f(1.f + (float)(W.fn + W.back_n)) * (1.f / 16.f);
+        case 3: return W.trimmed ? 1.f : 0.f;
+        case 4: return W.trimmed ? d2_pop / W.r2 : 0.f;
+        case 5: {
+            if (!W.trimmed) return 0.f;
+            const float nxt = W.fn > 0 ? key_d2(W.front[W.fn - 1]) : (W.back_n > 0 ? key_d2(W.wmark) : inf);
+            return fminf(nxt / (W.r2 * f), 4.f);
+        }
+        case 6: return fminf((float)(W.hops - W.last_change), 256.f) * (1.f / 16.f);
+        case 7: return W.hop_rins * 0.25f;
+        case 8: return adm * 0.125f;
+        case 9: return cnt * (1.f / 32.f);
+        case 10: return W.trimmed ? W.r2 / W.r2_first : 1.f;
+        default: return fminf((float)(W.evals - W.evals_change), 4096.f) * (1.f / 256.f);
+    }
+}
+
+// logit(stop) - logit(continue) of the 12-64-64-2 network; bfloat16 weights in shared memory,
+// inference layout W1t [12][64], b1, W2t [64][64], b2, W3 [2][64], b3. Warp-cooperative.
+__device__ float stop_margin(const __nv_bfloat16* w, const float* x, int lane) {
+    const __nv_bfloat16* W1t = w;
+    const __nv_bfloat16* b1 = W1t + 12 * 64;
+    const __nv_bfloat16* W2t = b1 + 64;
+    const __nv_bfloat16* b2 = W2t + 64 * 64;
+    const __nv_bfloat16* W3 = b2 + 64;
+    const __nv_bfloat16* b3 = W3 + 2 * 64;
+    float a0 = __bfloat162float(b1[lane]), a1 = __bfloat162float(b1[lane + 32]);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+        a0 = fmaf(__bfloat162float(W1t[i * 64 + lane]), x[i], a0);
+        a1 = fmaf(__bfloat162float(W1t[i * 64 + lane + 32]), x[i], a1);
+    }
+    a0 = fmaxf(a0, 0.f);
+    a1 = fmaxf(a1, 0.f);
+    float c0 = __bfloat162float(b2[lane]), c1 = __bfloat162float(b2[lane + 32]);
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        const float v = __shfl_sync(0xffffffffu, a0, i);
+        c0 = fmaf(__bfloat162float(W2t[i * 64 + lane]), v, c0);
+        c1 = fmaf(__bfloat162float(W2t[i * 64 + lane + 32]), v, c1);
+    }
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        const float v = __shfl_sync(0xffffffffu, a1, i);
+        c0 = fmaf(__bfloat162float(W2t[(32 + i) * 64 + lane]), v, c0);
+        c1 = fmaf(__bfloat162float(W2t[(32 + i) * 64 + lane + 32]), v, c1);
+    }
+    c0 = fmaxf(c0, 0.f);
+    c1 = fmaxf(c1, 0.f);
+    float p = (__bfloat162float(W3[64 + lane]) - __bfloat162float(W3[lane])) * c0 +
+              (__bfloat162float(W3[64 + lane + 32]) - __bfloat162float(W3[lane + 32])) * c1;
+#pragma unroll
+    for (int m = 16; m; m >>= 1) p += __shfl_xor_sync(0xffffffffu, p, m);
+    return p + __bfloat162float(b3[1]) - __bfloat162float(b3[0]);
 }
 
 // Append to the back pool; on a full pool drop keys above thr first. False if still full.
@@ -482,6 +563,12 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
         P.ids[(int64_t)q * P.k + i] = ok ? __ldg(P.new2old + key_id(v)) : -1;
         P.dists[(int64_t)q * P.k + i] = ok ? sqrtf(key_d2(v)) : __int_as_float(0x7f800000);
     }
+    if (P.rec_feats) {
+        // label of the hop recorded in slot t (hop t+1): 1 if R never changed after that hop
+        const int rec = min(W.hops, P.rec_cap);
+        for (int t = lane; t < rec; t += 32) P.rec_labels[(int64_t)q * P.rec_cap + t] = (t + 1 >= W.last_change) ? 1 : 0;
+        if (lane == 0) P.rec_counts[q] = rec;
+    }
     if (lane == 0) {
         if (P.status) P.status[q] = status;
         if (P.trace) {
@@ -509,6 +596,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     W.trimmed = false;
     W.r2 = __int_as_float(0x7f800000);
     W.hops = W.evals = W.peak = 0;
+    W.last_change = W.evals_change = W.hop_rins = 0;
+    W.r2_first = 1.f;
     __syncwarp();
     if (!seed_ok) {                                            // bad seed / vertex id
         finish_query(P, W, q, qv_smem, DEG_EINVAL, tier, lane);
@@ -575,6 +664,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         // 4. admit against the radius from before the hop
         const float r2pre = W.trimmed ? W.r2 : inf;
         const float thrpre = W.trimmed ? W.r2 * P.f : inf;
+        int adm = 0;
+        W.hop_rins = 0;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < cnt;
@@ -586,6 +677,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
             unsigned sm = __ballot_sync(0xffffffffu, toS);
             unsigned rm = __ballot_sync(0xffffffffu, valid && d2 <= r2pre);
+            adm += __popc(sm);
             __syncwarp();
             while (sm) {
                 const int src = __ffs(sm) - 1;
@@ -600,6 +692,19 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         W.peak = max(W.peak, W.fn + W.back_n);
         __syncwarp();
+        if (P.learned || P.rec_feats) {
+            float x[kStopFeatures];
+#pragma unroll
+            for (int i = 0; i < kStopFeatures; ++i) x[i] = stop_feature(W, i, key_d2(m), cnt, adm, P.f);
+            if (P.rec_feats && W.hops <= P.rec_cap && lane < kStopFeatures) {
+                float v = x[0];
+#pragma unroll
+                for (int i = 1; i < kStopFeatures; ++i) v = lane == i ? x[i] : v;
+                P.rec_feats[((int64_t)q * P.rec_cap + (W.hops - 1)) * kStopFeatures + lane] = v;
+            }
+            // learned stop, evaluated every other hop (the network costs about as much as a hop)
+            if (P.learned && (W.hops & 1) == 0 && stop_margin(P.stop_w, x, lane) > P.stop_logit) break;
+        }
     }
     finish_query(P, W, q, qv_smem, status, tier, lane);
     return true;
@@ -619,13 +724,26 @@ __device__ __forceinline__ float* bind_smem(WarpState& W, uint8_t* base, const P
     return W.cd2 + kMaxDegree;
 }
 
+// Bytes of shared memory for the learned-stop weights at the head of a block (0 if off).
+__host__ __device__ inline int64_t stop_bytes(int learned) { return learned ? (2ll * kStopParams + 15) / 16 * 16 : 0; }
+
+__device__ __forceinline__ uint8_t* load_stop_weights(Params& P, uint8_t* smem) {
+    if (!P.learned) return smem;
+    __nv_bfloat16* w = reinterpret_cast<__nv_bfloat16*>(smem);
+    for (int i = threadIdx.x; i < kStopParams; i += blockDim.x) w[i] = P.stop_w[i];
+    __syncthreads();
+    P.stop_w = w;
+    return smem + stop_bytes(1);
+}
+
 template <class Rows, int G, int CPL>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = blockIdx.x * P.wpb + warp;
+    uint8_t* wbase = load_stop_weights(P, smem);
     WarpState W;
-    float* qv = bind_smem(W, smem + warp * warp_bytes(P.kcap, P.dim), P);
+    float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
     W.bitmap = P.bitmaps + (int64_t)slot * P.words;
     W.back = P.backs + (int64_t)slot * P.bstride;
     W.bcap = P.bcap;
@@ -644,9 +762,10 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_device_kernel(Para
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int slot = blockIdx.x * kWarpsPerBlock + warp;
+    uint8_t* wbase = load_stop_weights(P, smem);
     if (slot >= P.pslots) return;
     WarpState W;
-    float* qv = bind_smem(W, smem + warp * warp_bytes(P.kcap, P.dim), P);
+    float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
     W.bitmap = P.pbitmaps + (int64_t)slot * P.words;
     W.back = P.pbacks + (int64_t)slot * (P.n + 1);
     W.bcap = (int32_t)(P.n + 1);
@@ -668,11 +787,11 @@ int launch_typed(Params P, cudaStream_t st, std::string* why) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t wb = warp_bytes(P.kcap, P.dim);
-    if (wb > smem_max) return *why = "search state does not fit in shared memory", (int)cudaErrorInvalidValue;
-    const int wpb = (int)std::min<int64_t>(kWarpsPerBlock, smem_max / wb);
+    const int64_t wb = warp_bytes(P.kcap, P.dim), sb = stop_bytes(P.learned);
+    if (wb + sb > smem_max) return *why = "search state does not fit in shared memory", (int)cudaErrorInvalidValue;
+    const int wpb = (int)std::min<int64_t>(kWarpsPerBlock, (smem_max - sb) / wb);
     P.wpb = wpb;
-    const int64_t smem = wb * wpb;
+    const int64_t smem = sb + wb * wpb;
     auto fk = search_fast_kernel<Rows, G, CPL>;
     if ((e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return *why = std::string("shared memory attribute: ") + cudaGetErrorString(e), (int)e;
@@ -686,7 +805,7 @@ int launch_typed(Params P, cudaStream_t st, std::string* why) {
     fk<<<(unsigned)grid, wpb * 32, smem, st>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return *why = std::string("main kernel: ") + cudaGetErrorString(e), (int)e;
     auto dk = search_device_kernel<Rows, G, CPL>;
-    const int64_t dsm = wb * kWarpsPerBlock;
+    const int64_t dsm = sb + wb * kWarpsPerBlock;
     if (dsm > smem_max) return *why = "second kernel state does not fit", (int)cudaErrorInvalidValue;
     if ((e = cudaFuncSetAttribute(dk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm)) != cudaSuccess)
         return *why = "second kernel attribute", (int)e;
@@ -808,6 +927,14 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.rerank = reduced ? 1 : 0;
     P.f = (float)((1.0 + (double)a.eps) * (1.0 + (double)a.eps));
     P.max_hops = a.max_hops;
+    P.learned = a.learned_stop ? 1 : 0;
+    P.stop_w = reinterpret_cast<const __nv_bfloat16*>(ix.stop_w);
+    P.stop_logit = ix.stop_logit;
+    if (P.learned && !P.stop_w) return *why = "no stop model set for this index", (int)cudaErrorInvalidValue;
+    P.rec_feats = a.rec_feats;
+    P.rec_labels = a.rec_labels;
+    P.rec_counts = a.rec_counts;
+    P.rec_cap = a.rec_cap;
     P.ids = a.ids;
     P.dists = a.dists;
     P.status = a.status;

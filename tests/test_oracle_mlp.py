@@ -1,0 +1,49 @@
+"""Pins for the oracle of the learned early-stop network (not from the paper; a plain MLP with a
+softmax cross-entropy loss): its analytic gradient against central finite differences in FP64,
+and closed forms for the loss."""
+import numpy as np
+
+import oracle
+
+
+def _rand(seed=0, count=37):
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal(oracle.mlp_nparams()) * 0.3
+    x = rng.standard_normal((count, 12)).astype(np.float32)
+    y = rng.integers(0, 2, count).astype(np.int32)
+    return w, x, y
+
+
+def test_gradient_matches_finite_differences():
+    w, x, y = _rand()
+    _, g = oracle.mlp_loss_grad(w, x, y)
+    rng = np.random.default_rng(1)
+    idx = rng.choice(len(w), 300, replace=False)
+    h = 1e-6
+    for i in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (oracle.mlp_loss_grad(wp, x, y, False) - oracle.mlp_loss_grad(wm, x, y, False)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_zero_weights_give_log2_loss_and_half_probability():
+    # all parameters zero: z = 0 for every sample -> loss = log 2, p(stop) = 1/2, gradient only
+    # on the output bias: mean(softmax - onehot) = (1/2 - frac0, 1/2 - frac1)
+    _, x, y = _rand(2, 50)
+    w = np.zeros(oracle.mlp_nparams())
+    loss, g = oracle.mlp_loss_grad(w, x, y)
+    assert abs(loss - np.log(2)) < 1e-15
+    np.testing.assert_allclose(oracle.mlp_predict(w, x), 0.5)
+    frac1 = y.mean()
+    np.testing.assert_allclose(g[-2:], [0.5 - (1 - frac1), 0.5 - frac1], atol=1e-15)
+    assert np.all(g[:-2] == 0)
+
+
+def test_output_bias_alone_sets_the_probability():
+    # only b3 non-zero: z = b3 -> p(stop) = sigmoid(b3[1] - b3[0])
+    _, x, y = _rand(3, 10)
+    w = np.zeros(oracle.mlp_nparams())
+    w[-2:] = [0.25, 1.5]
+    np.testing.assert_allclose(oracle.mlp_predict(w, x), 1 / (1 + np.exp(-1.25)), rtol=1e-14)

@@ -241,6 +241,44 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+SERVE_RATES = (50_000, 100_000, 200_000, 500_000)
+SERVE_REQUESTS = 100_000
+
+
+def serving(deg, idx, w, q, gt):
+    """Continuous batching over the 1M x 128 index stored in bfloat16: Poisson arrivals at each
+    rate, k uniform in {1, 10, 100}, eps uniform in {0.05, 0.1, 0.2}, 20% exploration requests.
+    Reports p50/p99 latency (arrival to completion seen by the host), sustained QPS and recall@10
+    of the vector requests with k >= 10."""
+    rng = np.random.default_rng(4)
+    out = {"index": "bf16 rows + re-rank, pivot entry", "requests_per_rate": SERVE_REQUESTS, "rates": {}}
+    srv = deg.Server(idx, capacity=1 << 16, kmax=100, precision="bf16", entry="pivot", idle_timeout_s=60.0)
+    out["slots"] = srv.slots
+    try:
+        for rate in SERVE_RATES:
+            n = SERVE_REQUESTS
+            ks = rng.choice([1, 10, 100], n).astype(np.int32)
+            epss = rng.choice([0.05, 0.1, 0.2], n).astype(np.float32)
+            explore = rng.random(n) < 0.2
+            vertices = np.where(explore, rng.integers(0, w.n, n), -1).astype(np.int32)
+            qi = rng.integers(0, len(q), n)
+            arrivals = synth.poisson_arrivals(rate, n, seed=4 + rate)
+            arrivals -= arrivals[0]
+            t0 = time.perf_counter()
+            lat, ids, _, st = srv.run_trace(q[qi], vertices, ks, epss, arrivals, timeout_s=300.0)
+            wall = time.perf_counter() - t0
+            vec10 = (~explore) & (ks >= 10)
+            rec = recall(ids[vec10, :10], gt[qi[vec10]])
+            out["rates"][str(rate)] = {"offered_qps": rate, "sustained_qps": n / wall, "p50_ms": 1e3 * float(np.median(lat)),
+                                       "p99_ms": 1e3 * float(np.percentile(lat, 99)), "recall_at_10": rec,
+                                       "status_ok": bool((st == 0).all())}
+            log(f"[bench] serving {rate}/s: sustained {n / wall:.0f}/s, p50 {1e3 * np.median(lat):.2f} ms, "
+                f"p99 {1e3 * np.percentile(lat, 99):.2f} ms, recall@10 {rec:.4f}")
+    finally:
+        srv.stop()
+    return out
+
+
 # eps at which the plain float32 search reaches recall@10 >= 0.95 on this workload (from the
 # sweep the GPU arm runs at start-up; the reference arm uses it so both arms do the same work)
 OPERATING_EPS = 0.08
@@ -254,6 +292,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
@@ -391,6 +430,8 @@ def main():
         "gpu_launches": (4 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
         "clocks": clk,
     }
+    if not args.no_serve:
+        line["serving"] = serving(deg, idx, w, q, gt)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         line["cpu_baseline"] = cpu_baseline(base, idx.adjacency(), q, oracle.median_vertex(base), plain["eps"])

@@ -206,6 +206,59 @@ DEG_API deg_status deg_mlp_predict(const float* w_dev, const float* x_dev, int64
  * decision threshold: stop when P(stop) > threshold, 0 < threshold < 1. */
 DEG_API deg_status deg_set_stop_model(deg_index* idx, const float* w_dev, float threshold, void* stream);
 
+/* ---- serving (library extension: continuous batching) ---------------------------------------
+ * A persistent kernel keeps the index resident and serves requests from a ring in mapped host
+ * memory: each of its warps takes the next request as soon as it is free, so requests posted
+ * while others run are admitted as warps free up and run concurrently with them. Requests mix
+ * k, eps and kind (vector query or exploration from a vertex). A request's result equals the
+ * result of the same search run alone (the same per-query code; nothing is shared between
+ * queries). Every device wait is bounded: when no request arrives for idle_timeout_s the kernel
+ * ends and deg_serve_stop reports DEG_ETIMEOUT. */
+
+typedef struct deg_server deg_server;
+
+typedef struct {
+    int32_t capacity;        /* ring slots (requests posted and not yet collected), >= 1          */
+    int32_t kmax;            /* largest k of any request, 1..1024                                 */
+    int32_t precision;       /* DEG_F32 | DEG_BF16 | DEG_FP8 (uploaded)                           */
+    int32_t rerank;          /* reduced precision: re-rank width (0 = k)                          */
+    int32_t entry_mode;      /* vector requests: 0 fixed entry vertex, 1 nearest pivot            */
+    int32_t learned_stop;    /* 1: use the index's stop network                                    */
+    double idle_timeout_s;   /* end the kernel when no request arrives for this long (> 0)         */
+} deg_serve_config;
+
+/* Launch the serving kernel on its own stream. The index must stay alive until deg_serve_stop. */
+DEG_API deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cfg, deg_server** out);
+
+/* Post one request: vec_host [dim] float32 for a vector query (vertex = -1), or vec_host NULL
+ * and vertex = a vertex id for an exploration request; 1 <= k <= kmax; eps >= 0. *seq_out gets
+ * its sequence number. DEG_EOVERFLOW (nothing posted) when its ring slot still holds an
+ * uncollected request: poll earlier requests and retry. */
+DEG_API deg_status deg_serve_submit(deg_server* srv, const float* vec_host, int32_t vertex, int32_t k, float eps,
+                                    int64_t* seq_out);
+
+/* 1 and the result (ids_host / dists_host [k], status_host [1], each nullable) if request seq is
+ * finished, 0 if not yet, negative deg_status on error. Collecting frees its ring slot. */
+DEG_API int32_t deg_serve_poll(deg_server* srv, int64_t seq, int32_t* ids_host, float* dists_host,
+                               int32_t* status_host);
+
+/* Replay a request trace: request i is posted at arrival_s[i] seconds after the call starts (or
+ * as soon as its ring slot frees), results go to ids_out / dists_out [count][kmax] and
+ * status_out [count], and latency_s_out[i] = completion time - arrival_s[i] as seen by the host.
+ * vecs_host [count][dim] (rows of exploration requests are ignored), vertices [count] (-1 for a
+ * vector query), ks [count], epss [count]. Fails with DEG_ETIMEOUT after timeout_s seconds. */
+DEG_API deg_status deg_serve_run_trace(deg_server* srv, const float* vecs_host, const int32_t* vertices,
+                                       const int32_t* ks, const float* epss, const double* arrival_s, int64_t count,
+                                       double* latency_s_out, int32_t* ids_out, float* dists_out,
+                                       int32_t* status_out, double timeout_s);
+
+/* Number of warps (concurrent requests) of the running kernel. */
+DEG_API int32_t deg_serve_slots(const deg_server* srv);
+
+/* Ask the kernel to finish, wait for it (bounded: in-flight requests complete first), free the
+ * server. Returns DEG_OK, or DEG_ETIMEOUT if the kernel had ended on its idle timeout. */
+DEG_API deg_status deg_serve_stop(deg_server* srv);
+
 /* ---- exact ground truth (Eq. 1) ----------------------------------------------------------- */
 
 /* Exact k nearest neighbours of queries_dev [nq][dim] among base_dev [n][dim] (float32 rows,

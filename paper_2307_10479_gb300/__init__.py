@@ -43,6 +43,12 @@ class SearchParams(ctypes.Structure):
                 ("queue_cap", ctypes.c_int32), ("entry_mode", ctypes.c_int32), ("learned_stop", ctypes.c_int32)]
 
 
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int32), ("kmax", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("rerank", ctypes.c_int32), ("entry_mode", ctypes.c_int32), ("learned_stop", ctypes.c_int32),
+                ("idle_timeout_s", ctypes.c_double)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -81,6 +87,12 @@ def lib() -> ctypes.CDLL:
             "deg_mlp_adam": (S, [P, P, P, P, i32, f32, P]),
             "deg_mlp_predict": (S, [P, P, i64, P, P]),
             "deg_set_stop_model": (S, [P, P, f32, P]),
+            "deg_serve_start": (S, [P, ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]),
+            "deg_serve_submit": (S, [P, P, i32, i32, f32, ctypes.POINTER(i64)]),
+            "deg_serve_poll": (i32, [P, i64, P, P, P]),
+            "deg_serve_run_trace": (S, [P, P, P, P, P, P, i64, P, P, P, P, ctypes.c_double]),
+            "deg_serve_slots": (i32, [P]),
+            "deg_serve_stop": (S, [P]),
             "deg_last_error": (ctypes.c_char_p, []),
         }
         for name, (res, args) in sig.items():
@@ -260,6 +272,61 @@ class Index:
         import torch
         weights = _require_cuda(weights, torch.float32, "weights")
         _check(lib().deg_set_stop_model(self._h, _dptr(weights), float(threshold), _stream_ptr(stream)))
+
+
+class Server:
+    """Continuous-batching server: a persistent kernel serving requests posted to a ring."""
+
+    def __init__(self, index: "Index", capacity: int = 65536, kmax: int = 128, precision: str = "f32",
+                 rerank: int = 0, entry: str = "fixed", learned_stop: bool = False, idle_timeout_s: float = 30.0):
+        self.index = index
+        self.kmax = kmax
+        self.dim = index.info()[1]
+        cfg = ServeConfig(capacity, kmax, PRECISIONS[precision], rerank, {"fixed": 0, "pivot": 1}[entry],
+                          1 if learned_stop else 0, float(idle_timeout_s))
+        self._h = ctypes.c_void_p()
+        _check(lib().deg_serve_start(index._h, ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    @property
+    def slots(self) -> int:
+        return int(lib().deg_serve_slots(self._h))
+
+    def submit(self, vec=None, vertex: int = -1, k: int = 10, eps: float = 0.1) -> int:
+        seq = ctypes.c_int64()
+        v = None if vec is None else np.ascontiguousarray(vec, np.float32)
+        _check(lib().deg_serve_submit(self._h, None if v is None else v.ctypes.data, vertex, k, float(eps),
+                                      ctypes.byref(seq)))
+        return seq.value
+
+    def poll(self, seq: int, k: int):
+        ids = np.empty(k, np.int32)
+        d = np.empty(k, np.float32)
+        st = ctypes.c_int32()
+        got = lib().deg_serve_poll(self._h, seq, ids.ctypes.data, d.ctypes.data, ctypes.byref(st))
+        if got < 0:
+            _check(got)
+        return (ids, d, st.value) if got == 1 else None
+
+    def run_trace(self, vecs, vertices, ks, epss, arrival_s, timeout_s: float = 120.0):
+        vecs = np.ascontiguousarray(vecs, np.float32)
+        vertices = np.ascontiguousarray(vertices, np.int32)
+        ks = np.ascontiguousarray(ks, np.int32)
+        epss = np.ascontiguousarray(epss, np.float32)
+        arrival_s = np.ascontiguousarray(arrival_s, np.float64)
+        n = len(ks)
+        lat = np.empty(n, np.float64)
+        ids = np.full((n, self.kmax), -1, np.int32)
+        d = np.full((n, self.kmax), np.inf, np.float32)
+        st = np.empty(n, np.int32)
+        _check(lib().deg_serve_run_trace(self._h, vecs.ctypes.data, vertices.ctypes.data, ks.ctypes.data,
+                                         epss.ctypes.data, arrival_s.ctypes.data, n, lat.ctypes.data, ids.ctypes.data,
+                                         d.ctypes.data, st.ctypes.data, float(timeout_s)))
+        return lat, ids, d, st
+
+    def stop(self):
+        h, self._h = self._h, None
+        if h:
+            _check(lib().deg_serve_stop(h))
 
 
 STOP_FEATURES, STOP_PARAMS = 12, 5122

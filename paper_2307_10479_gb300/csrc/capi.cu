@@ -3,11 +3,14 @@
 // checks, allocates, copies and launches.
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "deg_internal.h"
@@ -548,4 +551,205 @@ extern "C" deg_status deg_set_stop_model(deg_index* idx, const float* w_dev, flo
     idx->dev.stop_logit = std::log(threshold / (1.f - threshold));
     if ((e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream))) != cudaSuccess) return cuda_fail(e, "set_stop_model");
     return DEG_OK;
+}
+
+// ---- serving ------------------------------------------------------------------------------------
+
+struct deg_server {
+    deg_index* idx = nullptr;
+    cudaStream_t stream = nullptr;
+    int32_t cap = 0, kmax = 0, dim = 0, warps = 0;
+    // mapped pinned host memory (host views)
+    float* vecs = nullptr;
+    int32_t* meta = nullptr;               // [cap][4]
+    int32_t* ids = nullptr;
+    float* dists = nullptr;
+    int32_t* status = nullptr;
+    int32_t* trace = nullptr;
+    uint32_t* done = nullptr;
+    unsigned long long* tail = nullptr;
+    int32_t* stop = nullptr;
+    // device words
+    int32_t* kstatus = nullptr;
+    unsigned long long* claim = nullptr;
+    int64_t posted = 0;
+    std::vector<int64_t> held;             // per slot: sequence number occupying it, -1 if free
+};
+
+namespace {
+
+void server_free(deg_server* s) {
+    cudaFreeHost(s->vecs); cudaFreeHost(s->meta); cudaFreeHost(s->ids); cudaFreeHost(s->dists);
+    cudaFreeHost(s->status); cudaFreeHost(s->trace); cudaFreeHost(s->done); cudaFreeHost(s->tail);
+    cudaFreeHost(s->stop);
+    cudaFree(s->kstatus); cudaFree(s->claim);
+    if (s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+template <class T>
+cudaError_t host_alloc(T** p, size_t count) {
+    cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(p), sizeof(T) * count, cudaHostAllocMapped);
+    if (e == cudaSuccess) std::memset(*p, 0, sizeof(T) * count);
+    return e;
+}
+
+template <class T>
+T* dev_view(T* host) {
+    void* d = nullptr;
+    cudaHostGetDevicePointer(&d, host, 0);
+    return static_cast<T*>(d);
+}
+
+}  // namespace
+
+extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cfg, deg_server** out) {
+    if (!out) return fail(DEG_EINVAL, "serve_start: out is NULL");
+    *out = nullptr;
+    if (!idx || !cfg) return fail(DEG_EINVAL, "serve_start: NULL argument");
+    if (!idx->dev.x32) return fail(DEG_ENOTREADY, "serve_start: index not uploaded");
+    if (cfg->capacity < 1 || cfg->kmax < 1 || cfg->kmax > 1024 || !(cfg->idle_timeout_s > 0))
+        return fail(DEG_EINVAL, "serve_start: need capacity >= 1, 1 <= kmax <= 1024, idle_timeout_s > 0");
+    if (cfg->precision < DEG_F32 || cfg->precision > DEG_FP8 || !(idx->uploaded_mask & (1 << cfg->precision)))
+        return fail(DEG_ENOTREADY, "serve_start: precision copy not uploaded");
+    if (cfg->entry_mode != 0 && cfg->entry_mode != 1) return fail(DEG_EINVAL, "serve_start: entry_mode must be 0 or 1");
+    if (cfg->learned_stop && !idx->dev.stop_w) return fail(DEG_ENOTREADY, "serve_start: no stop model");
+    if (cfg->rerank < 0 || cfg->rerank > 1024) return fail(DEG_EINVAL, "serve_start: rerank out of range");
+    std::string why;
+    if (workspace_reserve(idx->ws, idx->dev, 1, &why) != 0) return fail(DEG_ENOMEM, "serve_start: workspace: " + why);
+    deg_server* s = new (std::nothrow) deg_server;
+    if (!s) return fail(DEG_ENOMEM, "serve_start: host allocation failed");
+    s->idx = idx;
+    s->cap = cfg->capacity;
+    s->kmax = cfg->kmax;
+    s->dim = idx->dim;
+    cudaError_t e;
+    const size_t cap = (size_t)s->cap;
+    if ((e = host_alloc(&s->vecs, cap * s->dim)) != cudaSuccess || (e = host_alloc(&s->meta, cap * 4)) != cudaSuccess ||
+        (e = host_alloc(&s->ids, cap * s->kmax)) != cudaSuccess || (e = host_alloc(&s->dists, cap * s->kmax)) != cudaSuccess ||
+        (e = host_alloc(&s->status, cap)) != cudaSuccess || (e = host_alloc(&s->trace, cap * 4)) != cudaSuccess ||
+        (e = host_alloc(&s->done, cap)) != cudaSuccess || (e = host_alloc(&s->tail, 1)) != cudaSuccess ||
+        (e = host_alloc(&s->stop, 1)) != cudaSuccess || (e = cudaMalloc(&s->kstatus, 4)) != cudaSuccess ||
+        (e = cudaMalloc(&s->claim, 8)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        server_free(s);
+        return fail(DEG_ENOMEM, std::string("serve_start: ") + cudaGetErrorString(e));
+    }
+    s->held.assign(cap, -1);
+    if ((e = cudaMemsetAsync(s->kstatus, 0, 4, s->stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(s->claim, 0, 8, s->stream)) != cudaSuccess) {
+        server_free(s);
+        return cuda_fail(e, "serve_start");
+    }
+    ServeArgs a{&idx->dev, dev_view(s->vecs), dev_view(s->meta), dev_view(s->ids), dev_view(s->dists),
+                dev_view(s->status), dev_view(s->trace), dev_view(s->done), dev_view(s->tail), dev_view(s->stop),
+                s->kstatus, s->claim, s->cap, s->kmax, cfg->entry_mode, cfg->precision, cfg->rerank,
+                cfg->learned_stop ? 1 : 0, (unsigned long long)(cfg->idle_timeout_s * 1e9)};
+    if (launch_serving(a, idx->ws, reinterpret_cast<deg_stream_t>(s->stream), &s->warps, &why) != 0) {
+        server_free(s);
+        return fail(DEG_ECUDA, "serve_start: " + why);
+    }
+    *out = s;
+    return DEG_OK;
+}
+
+extern "C" int32_t deg_serve_slots(const deg_server* srv) { return srv ? srv->warps : 0; }
+
+extern "C" deg_status deg_serve_submit(deg_server* s, const float* vec_host, int32_t vertex, int32_t k, float eps,
+                                       int64_t* seq_out) {
+    if (!s || !seq_out) return fail(DEG_EINVAL, "serve_submit: NULL argument");
+    if (k < 1 || k > s->kmax || !(eps >= 0.f) || std::isinf(eps)) return fail(DEG_EINVAL, "serve_submit: bad k or eps");
+    if (vertex >= 0 ? (vertex >= s->idx->n || vec_host) : (!vec_host || vertex != -1))
+        return fail(DEG_EINVAL, "serve_submit: give a vector (vertex -1) or a vertex id (vector NULL)");
+    if (vertex >= 0 && k > s->idx->n - 1) return fail(DEG_EINVAL, "serve_submit: k larger than the candidates");
+    const int64_t seq = s->posted;
+    const size_t r = (size_t)(seq % s->cap);
+    if (s->held[r] >= 0) return fail(DEG_EOVERFLOW, "serve_submit: ring slot busy (collect earlier results)");
+    if (vec_host) std::memcpy(s->vecs + r * s->dim, vec_host, sizeof(float) * s->dim);
+    int32_t eb;
+    std::memcpy(&eb, &eps, 4);
+    s->meta[4 * r + 0] = k;
+    s->meta[4 * r + 1] = eb;
+    s->meta[4 * r + 2] = vertex;
+    s->meta[4 * r + 3] = (int32_t)seq;
+    s->held[r] = seq;
+    ++s->posted;
+    std::atomic_thread_fence(std::memory_order_release);
+    __atomic_store_n(s->tail, (unsigned long long)s->posted, __ATOMIC_RELEASE);
+    *seq_out = seq;
+    return DEG_OK;
+}
+
+extern "C" int32_t deg_serve_poll(deg_server* s, int64_t seq, int32_t* ids_host, float* dists_host,
+                                  int32_t* status_host) {
+    if (!s || seq < 0 || seq >= s->posted) return fail(DEG_EINVAL, "serve_poll: unknown request");
+    const size_t r = (size_t)(seq % s->cap);
+    if (s->held[r] != seq) return fail(DEG_EINVAL, "serve_poll: request already collected");
+    if (__atomic_load_n(s->done + r, __ATOMIC_ACQUIRE) != (uint32_t)(seq + 1)) return 0;
+    const int32_t k = s->meta[4 * r + 0];
+    if (ids_host) std::memcpy(ids_host, s->ids + r * s->kmax, sizeof(int32_t) * k);
+    if (dists_host) std::memcpy(dists_host, s->dists + r * s->kmax, sizeof(float) * k);
+    if (status_host) *status_host = s->status[r];
+    s->held[r] = -1;
+    return 1;
+}
+
+extern "C" deg_status deg_serve_run_trace(deg_server* s, const float* vecs_host, const int32_t* vertices,
+                                          const int32_t* ks, const float* epss, const double* arrival_s, int64_t count,
+                                          double* latency_s_out, int32_t* ids_out, float* dists_out,
+                                          int32_t* status_out, double timeout_s) {
+    if (!s || !vecs_host || !vertices || !ks || !epss || !arrival_s || !latency_s_out || count < 0)
+        return fail(DEG_EINVAL, "serve_run_trace: NULL argument");
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    std::vector<int64_t> seq_of(count, -1);
+    std::vector<int64_t> outstanding;
+    outstanding.reserve(1 << 16);
+    int64_t next = 0, finished = 0;
+    while (finished < count) {
+        const double t = now();
+        if (t > timeout_s) return fail(DEG_ETIMEOUT, "serve_run_trace: trace did not finish in time");
+        // post every request whose arrival time has come (while ring slots are free)
+        while (next < count && arrival_s[next] <= t) {
+            int64_t seq;
+            const bool vq = vertices[next] < 0;
+            const deg_status st = deg_serve_submit(s, vq ? vecs_host + next * (int64_t)s->dim : nullptr,
+                                                   vq ? -1 : vertices[next], ks[next], epss[next], &seq);
+            if (st == DEG_EOVERFLOW) break;
+            if (st != DEG_OK) return st;
+            seq_of[next] = seq;
+            outstanding.push_back(next);
+            ++next;
+        }
+        // collect finished requests
+        for (size_t j = 0; j < outstanding.size();) {
+            const int64_t i = outstanding[j];
+            int32_t stv = 0;
+            const int32_t got = deg_serve_poll(s, seq_of[i], ids_out ? ids_out + i * s->kmax : nullptr,
+                                               dists_out ? dists_out + i * s->kmax : nullptr, &stv);
+            if (got < 0) return (deg_status)got;
+            if (got == 1) {
+                latency_s_out[i] = now() - arrival_s[i];
+                if (status_out) status_out[i] = stv;
+                ++finished;
+                outstanding[j] = outstanding.back();
+                outstanding.pop_back();
+            } else {
+                ++j;
+            }
+        }
+    }
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_serve_stop(deg_server* s) {
+    if (!s) return fail(DEG_EINVAL, "serve_stop: NULL server");
+    __atomic_store_n(s->stop, 1, __ATOMIC_RELEASE);
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    int32_t ks = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&ks, s->kstatus, 4, cudaMemcpyDeviceToHost);
+    server_free(s);
+    if (e != cudaSuccess) return cuda_fail(e, "serve_stop");
+    return ks == DEG_ETIMEOUT ? fail(DEG_ETIMEOUT, "serve_stop: the kernel ended on its idle timeout") : DEG_OK;
 }

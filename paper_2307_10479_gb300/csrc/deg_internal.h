@@ -95,7 +95,26 @@ struct SearchArgs {
     int32_t* trace;
 };
 
+// Serving ring (device pointers into mapped host memory, plus two device words).
+struct ServeArgs {
+    const DeviceIndex* ix;
+    const float* vecs;
+    const int32_t* meta;          // [cap][4] {k, eps bits, vertex, seq}
+    int32_t* ids;
+    float* dists;
+    int32_t* status;
+    int32_t* trace;
+    uint32_t* done;
+    const unsigned long long* tail;
+    const int32_t* stop;
+    int32_t* kstatus;
+    unsigned long long* claim;
+    int32_t cap, kmax, entry_mode, precision, rerank, learned_stop;
+    unsigned long long idle_ns;
+};
+
 // Kernel launchers (search.cu). Return a cudaError_t value (0 = success).
+int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* warps, std::string* why);
 int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::string* why);
 int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::string* why);
 void workspace_free(Workspace& ws);

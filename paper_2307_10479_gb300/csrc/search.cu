@@ -780,6 +780,165 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_device_kernel(Para
     }
 }
 
+// ---- serving: a persistent kernel over a request ring ----------------------------------------
+// Requests are posted by the host into a ring in mapped host memory; every warp of the kernel
+// claims the next request number, waits (bounded by %globaltimer) until the host has posted it,
+// runs it with the same per-query code as a batch search (so a request's result does not depend
+// on what else is in flight), writes the result into the ring and publishes it with a release
+// store of its sequence number. The kernel ends when the host raises the stop flag, or with
+// DEG_ETIMEOUT when no request arrives for idle_ns.
+struct ServeRing {
+    const float* vecs;                    // [cap][dim] query vectors
+    const int4* meta;                     // [cap] {k, eps bits, vertex (-1: vector query), seq}
+    int32_t* ids;                         // [cap][kmax]
+    float* dists;                         // [cap][kmax]
+    int32_t* status;                      // [cap]
+    int32_t* trace;                       // [cap][4]
+    uint32_t* done;                       // [cap]: seq + 1 once the result is written
+    const unsigned long long* tail;       // requests posted so far
+    const int32_t* stop;
+    int32_t* kstatus;                     // kernel status (device memory)
+    unsigned long long* claim;            // next request number (device memory)
+    int32_t cap, kmax, entry_mode;
+    unsigned long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_sys(const int32_t* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Nearest pivot (float32 distance, tie -> lower pivot index) to the query in shared memory.
+__device__ int32_t route_one(const Params& P, const int32_t* pivots, int np, const float* qv, int lane) {
+    uint64_t best = kEmptyKey;
+    for (int p = lane; p < np; p += 32) best = min(best, make_key(exact_d2_lane(P.x32, P.dim_pad, __ldg(pivots + p), qv), p));
+    best = warp_min64(best);
+    return __ldg(pivots + key_id(best));
+}
+
+template <class Rows, int G, int CPL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kernel(Params P, ServeRing S,
+                                                                                  const int32_t* pivots, int np) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    __shared__ int32_t seed_s[kWarpsPerBlock];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int slot = blockIdx.x * P.wpb + warp;
+    uint8_t* wbase = load_stop_weights(P, smem);
+    WarpState W;
+    float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
+    W.bitmap = P.bitmaps + (int64_t)slot * P.words;
+    W.back = P.backs + (int64_t)slot * P.bstride;
+    W.bcap = P.bcap;
+    const int dim4 = (P.dim + 3) / 4 * 4;
+    for (;;) {
+        unsigned long long i = 0;
+        if (lane == 0) i = atomicAdd(S.claim, 1ull);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        // wait until request i is posted, the host asks to stop, or nothing arrives for idle_ns
+        const unsigned long long t0 = global_ns();
+        int state = 0;                                        // 1 posted, 2 stop, 3 timeout
+        while (state == 0) {
+            if (lane == 0) {
+                if (ld_acquire_sys(S.tail) > i) state = 1;
+                else if (ld_acquire_sys(S.stop)) state = 2;
+                else if (global_ns() - t0 > S.idle_ns) state = 3;
+            }
+            state = __shfl_sync(0xffffffffu, state, 0);
+            if (state == 0) __nanosleep(500);
+        }
+        if (state == 3 && lane == 0) atomicExch(S.kstatus, (int)DEG_ETIMEOUT);
+        if (state != 1) return;
+        const int r = (int)(i % (unsigned long long)S.cap);
+        const int4 m = S.meta[r];
+        Params Q = P;
+        Q.k = m.x;
+        Q.ks = P.rerank ? max(P.ks, m.x) : m.x;
+        Q.f = (1.f + __int_as_float(m.y)) * (1.f + __int_as_float(m.y));
+        Q.nq = 1;
+        Q.ids = S.ids + (int64_t)r * S.kmax;
+        Q.dists = S.dists + (int64_t)r * S.kmax;
+        Q.status = S.status + r;
+        Q.trace = S.trace + 4 * (int64_t)r;
+        Q.seeds_internal = 0;
+        if (m.z >= 0) {                                       // exploration from vertex m.z
+            Q.explore = 1;
+            Q.seeds = reinterpret_cast<const int32_t*>(S.meta + r) + 2;
+            Q.queries = nullptr;
+        } else {
+            Q.explore = 0;
+            Q.queries = S.vecs + (int64_t)r * P.dim;
+            Q.seeds = nullptr;
+            if (S.entry_mode == 1) {
+                for (int d = lane; d < dim4; d += 32) qv[d] = d < P.dim ? Q.queries[d] : 0.f;
+                __syncwarp();
+                const int32_t sd = route_one(P, pivots, np, qv, lane);
+                if (lane == 0) seed_s[warp] = sd;
+                __syncwarp();
+                Q.seeds = seed_s + warp;
+                Q.seeds_internal = 1;
+            }
+        }
+        if (!run_query<Rows, G, CPL>(Q, W, 0, qv, 0, lane)) {
+            for (int j = lane; j < m.x; j += 32) { Q.ids[j] = -1; Q.dists[j] = __int_as_float(0x7f800000); }
+            if (lane == 0) *Q.status = DEG_EOVERFLOW;
+        }
+        __syncwarp();
+        __threadfence_system();
+        if (lane == 0) st_release_sys(S.done + r, (uint32_t)(i + 1));
+    }
+}
+
+template <class Rows, int G, int CPL>
+int launch_serve(Params P, const ServeRing& S, const int32_t* pivots, int np, cudaStream_t st, int* warps,
+                 std::string* why) {
+    cudaError_t e;
+    int dev = 0, smem_max = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t wb = warp_bytes(P.kcap, P.dim), sb = stop_bytes(P.learned);
+    if (wb * kWarpsPerBlock + sb > smem_max) return *why = "serving state does not fit", (int)cudaErrorInvalidValue;
+    P.wpb = kWarpsPerBlock;
+    const int64_t smem = sb + wb * kWarpsPerBlock;
+    auto k = serve_kernel<Rows, G, CPL>;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+        return *why = std::string("serve attribute: ") + cudaGetErrorString(e), (int)e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarpsPerBlock * 32, (size_t)smem)) != cudaSuccess)
+        return *why = "occupancy query failed", (int)e;
+    // every block must be resident at once (persistent); never more warps than device slots
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)P.slots / kWarpsPerBlock));
+    *warps = (int)(grid * kWarpsPerBlock);
+    k<<<(unsigned)grid, kWarpsPerBlock * 32, smem, st>>>(P, S, pivots, np);
+    if ((e = cudaGetLastError()) != cudaSuccess) return *why = std::string("serve kernel: ") + cudaGetErrorString(e), (int)e;
+    return 0;
+}
+
+template <class Rows>
+int dispatch_serve(Params P, const ServeRing& S, const int32_t* pivots, int np, cudaStream_t st, int* warps,
+                   std::string* why) {
+    const int nc = P.nchunk;
+    if (nc <= 4) return launch_serve<Rows, 4, 1>(P, S, pivots, np, st, warps, why);
+    if (nc <= 8) return launch_serve<Rows, 8, 1>(P, S, pivots, np, st, warps, why);
+    if (nc <= 16) return launch_serve<Rows, 16, 1>(P, S, pivots, np, st, warps, why);
+    if (nc <= 32) return launch_serve<Rows, 32, 1>(P, S, pivots, np, st, warps, why);
+    *why = "serving supports rows of at most 512 bytes";
+    return (int)cudaErrorInvalidValue;
+}
+
 template <class Rows, int G, int CPL>
 int launch_typed(Params P, cudaStream_t st, std::string* why) {
     cudaError_t e;
@@ -969,6 +1128,60 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.nchunk = ix.dim_pad8 / 16;
     P.scale8 = ix.scale8;
     return dispatch_shape<FP8Rows>(P, st, why);
+}
+
+}  // namespace deg
+
+namespace deg {
+
+int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* warps, std::string* why) {
+    const DeviceIndex& ix = *a.ix;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (ix.degree > kMaxDegree) return *why = "degree above 128", (int)cudaErrorInvalidValue;
+    Params P{};
+    P.x32 = ix.x32;
+    P.dim_pad = ix.dim_pad;
+    P.adj = ix.adj;
+    P.degree = ix.degree;
+    P.deg_pad = ix.deg_pad;
+    P.n = ix.n;
+    P.entry = ix.entry_internal;
+    P.old2new = ix.old2new;
+    P.new2old = ix.new2old;
+    P.dim = ix.dim;
+    const bool reduced = a.precision != DEG_F32;
+    P.ks = reduced && a.rerank ? a.rerank : 0;
+    P.kcap = std::max(32, pow2_at_least(std::max(a.kmax, P.ks)));
+    P.rerank = reduced ? 1 : 0;
+    P.learned = a.learned_stop ? 1 : 0;
+    P.stop_w = reinterpret_cast<const __nv_bfloat16*>(ix.stop_w);
+    P.stop_logit = ix.stop_logit;
+    if (P.learned && !P.stop_w) return *why = "no stop model set for this index", (int)cudaErrorInvalidValue;
+    P.words = ws.words;
+    P.bitmaps = ws.bitmaps;
+    P.backs = ws.backs;
+    P.slots = ws.slots;
+    P.bstride = ws.bcap;
+    P.bcap = ws.bcap;
+    ServeRing S{a.vecs, reinterpret_cast<const int4*>(a.meta), a.ids, a.dists, a.status, a.trace, a.done, a.tail,
+                a.stop, a.kstatus, a.claim, a.cap, a.kmax, a.entry_mode, a.idle_ns};
+    if (a.precision == DEG_F32) {
+        P.rows = reinterpret_cast<const uint8_t*>(ix.x32);
+        P.row_bytes = 4ll * ix.dim_pad;
+        P.nchunk = ix.dim_pad / 4;
+        return dispatch_serve<F32Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
+    }
+    if (a.precision == DEG_BF16) {
+        P.rows = reinterpret_cast<const uint8_t*>(ix.xbf);
+        P.row_bytes = 2ll * ix.dim_pad16;
+        P.nchunk = ix.dim_pad16 / 8;
+        return dispatch_serve<BF16Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
+    }
+    P.rows = ix.x8;
+    P.row_bytes = ix.dim_pad8;
+    P.nchunk = ix.dim_pad8 / 16;
+    P.scale8 = ix.scale8;
+    return dispatch_serve<FP8Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
 }
 
 }  // namespace deg

@@ -141,9 +141,13 @@ int mlp_adam(float* w, float* m, float* v, const float* g, int step, float lr, d
 int mlp_predict(const float* w, const float* x, int64_t count, float* p_stop, deg_stream_t stream, std::string* why);
 int mlp_pack_inference(const float* w, uint16_t* out, deg_stream_t stream, std::string* why);
 
-// Exact kNN (knn_exact.cu).
+// Exact kNN: tensor-core distances with an exact float32 re-rank (knn_tc.cu); synchronises the
+// stream.
 int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
                      int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
+// The same result from CUDA-core float32 distances and a full radix select (knn_exact.cu).
+int launch_knn_simt(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
+                    int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
 // Same, on a fixed statically allocated scratch (no allocation in the call).
 int launch_knn_exact_noalloc(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
                              int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);

@@ -133,8 +133,8 @@ __global__ void __launch_bounds__(kSelThreads) select_topk_kernel(const float* _
 
 }  // namespace
 
-int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim, int32_t k,
-                     int32_t* ids, float* dists, deg_stream_t stream, std::string* why) {
+int launch_knn_simt(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim, int32_t k,
+                    int32_t* ids, float* dists, deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (k > n) return *why = "k larger than n", (int)cudaErrorInvalidValue;
     const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(2ll << 30) / (4 * n)));

@@ -44,3 +44,77 @@ def test_knn_exact_ragged_and_chunked_shapes():
     assert e_ids.shape == (0, 5)
     with pytest.raises(deg.DegError):
         deg.knn_exact(torch.from_numpy(base[:3]).cuda(), torch.from_numpy(q).cuda(), 5)
+
+
+# ---- the tensor-core path against the CUDA-core path ---------------------------------------
+# knn_exact computes distances with tcgen05 (bfloat16 operands, float32 accumulators), keeps every
+# row within a proven error bound of the k-th approximate distance and re-ranks those in float32;
+# knn_exact_noalloc computes every float32 distance on the CUDA cores. Both sum
+# fmaf(q_d - x_d, q_d - x_d, .) in dimension order and order ties by id, so they agree bit for bit.
+
+def _cuda_core(base, q, k):
+    import ctypes
+    import paper_2307_10479_gb300 as deg
+    ids = torch.empty((q.shape[0], k), dtype=torch.int32, device="cuda")
+    d = torch.empty((q.shape[0], k), dtype=torch.float32, device="cuda")
+    st = deg.lib().knn_exact_noalloc(ctypes.c_void_p(base.data_ptr()), base.shape[0], ctypes.c_void_p(q.data_ptr()),
+                                     q.shape[0], base.shape[1], k, ctypes.c_void_p(ids.data_ptr()),
+                                     ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == deg.DEG_OK, deg.lib().deg_last_error()
+    torch.cuda.synchronize()
+    return ids, d
+
+
+def _both(base, q, k):
+    import paper_2307_10479_gb300 as deg
+    b, qq = torch.from_numpy(np.ascontiguousarray(base)).cuda(), torch.from_numpy(np.ascontiguousarray(q)).cuda()
+    t_ids, t_d = deg.knn_exact(b, qq, k)
+    s_ids, s_d = _cuda_core(b, qq, k)
+    return t_ids.cpu().numpy(), t_d.cpu().numpy(), s_ids.cpu().numpy(), s_d.cpu().numpy()
+
+
+@pytest.mark.parametrize("n,dim,nq,k", [
+    (10_000, 32, 200, 1), (10_000, 32, 200, 10), (10_000, 32, 300, 100), (10_000, 32, 129, 256),
+    (1_001, 7, 67, 5),            # ragged everything; K padded from 7 to 64
+    (5_000, 65, 130, 10),         # K padded to 128: two chunks of 64
+    (3_000, 300, 50, 10),         # K = 320 > 256: the query tile is staged per chunk
+    (1, 16, 3, 1),                # a single row
+    (300, 24, 1, 300 // 2),       # n below one 256-row tile
+])
+def test_tensor_core_path_equals_cuda_core_path_on_float_data(n, dim, nq, k):
+    base = synth.uniform(n, dim, 11)
+    q = synth.uniform(nq, dim, 12)
+    t_ids, t_d, s_ids, s_d = _both(base, q, k)
+    assert np.array_equal(t_ids, s_ids)
+    assert np.array_equal(t_d.view(np.uint32), s_d.view(np.uint32))
+
+
+def test_tensor_core_path_signed_and_scaled_data():
+    # zero-mean data of large magnitude: approximate distances cancel |q|^2 + |x|^2 against 2 q.x
+    rng = np.random.default_rng(4)
+    base = (rng.standard_normal((8_000, 48)) * 1e3).astype(np.float32)
+    q = (rng.standard_normal((150, 48)) * 1e3).astype(np.float32)
+    t_ids, t_d, s_ids, s_d = _both(base, q, 10)
+    assert np.array_equal(t_ids, s_ids) and np.array_equal(t_d.view(np.uint32), s_d.view(np.uint32))
+
+
+def test_tensor_core_path_sampled_threshold_on_integer_rows():
+    # 100,000 SIFT-like rows: the threshold comes from every 4th row (32,768-row sample limit)
+    w = synth.scaled(synth.WORKLOADS["sift-1m-d128"], 100_000, 257)
+    base, q = w.base(), w.queries()
+    t_ids, t_d, s_ids, s_d = _both(base, q, 10)
+    assert np.array_equal(t_ids, s_ids) and np.array_equal(t_d.view(np.uint32), s_d.view(np.uint32))
+    o_ids, o_d = oracle.knn_bruteforce(base, q[:40], 10)
+    assert np.array_equal(t_ids[:40], o_ids)
+
+
+def test_tensor_core_path_all_ties_falls_back_exactly():
+    # 20,000 equal rows: every row is a candidate (more than the per-query buffer), so the query
+    # is recomputed on the CUDA cores; the answer is the k smallest ids.
+    base = np.tile(synth.uniform(1, 32, 3), (20_000, 1))
+    base[7] += 0.5                                      # one row farther away
+    q = synth.uniform(5, 32, 4)
+    t_ids, t_d, s_ids, s_d = _both(base, q, 20)
+    assert np.array_equal(t_ids, s_ids) and np.array_equal(t_d.view(np.uint32), s_d.view(np.uint32))
+    for row in t_ids:                                   # equal distances: the smallest ids
+        assert set(row.tolist()) <= set(range(21))

@@ -6,8 +6,10 @@
 //   1. bfloat16 copies of rows and queries (K padded to a multiple of 64), with float32 squared
 //      norms and the norms of the rounding residuals x - bf16(x);
 //   2. sample pass: approximate squared distances a = |q|^2 + |x|^2 - 2 bf16(q).bf16(x) of every
-//      query against every s-th row (tcgen05.mma.kind::f16, float32 accumulators in tensor memory);
-//      t_s = the k-th smallest of them is at least the k-th smallest a over all rows;
+//      query against every s-th row (tcgen05.mma.kind::f16, float32 accumulators in tensor memory),
+//      reduced to the minimum of each group of 16 sampled rows; t_s = the k-th smallest group
+//      minimum. k groups hold k distinct rows with a <= t_s, so t_s is at least the k-th smallest a
+//      over all rows;
 //   3. filter pass: a against every row; a row is a candidate when a <= t_s + 2b, where b bounds
 //      |a - e| for the float32 distance e (bfloat16 rounding, accumulation and norm rounding; see
 //      error_bound). If e_k is the k-th smallest e, the k rows with the smallest a have e <= t + b
@@ -17,9 +19,19 @@
 //      rows with a <= t + 2b get e computed exactly, sorted by (e, id), the first k returned.
 // A query with more candidates than the buffer holds is recomputed by the CUDA-core path.
 //
-// Tensor-core tile: M = 128 queries (tensor-memory lanes) x N = 256 rows (tensor-memory columns),
-// K staged 64 at a time in the no-swizzle K-major layout of 8-row x 16-byte core matrices. Two
-// CTAs per SM (shared memory sized for it) so that one stages while the other multiplies.
+// The distance kernel is a persistent, warp-specialised tcgen05 pipeline, one CTA per SM:
+//   warp 0  TMA producer: 128 queries x 64 and 256 rows x 64 bf16 tiles (128-byte swizzle) into a
+//           4-stage shared-memory ring, completion counted on the stage's mbarrier;
+//   warp 1  MMA issuer: one thread issues tcgen05.mma (M = 128, N = 256, K = 16) into one of two
+//           256-column tensor-memory accumulators, commits each stage back to the producer and each
+//           finished tile to the epilogue;
+//   warps 2-9  epilogue: tcgen05.ld of the finished accumulator (two warps per 32-lane quarter, 128
+//           columns each), approximate distances, group minima (sample pass) or candidate appends
+//           (filter pass), then the accumulator is handed back, so the next tile's MMAs overlap this
+//           epilogue.
+// Work items are (query tile, row tile) pairs, the query tile varying fastest, so the CTAs running
+// at one time read the same row tiles (each row tile leaves DRAM once, the rest are L2 hits).
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -32,16 +44,18 @@
 namespace deg {
 namespace {
 
-constexpr int TM = 128, TN = 256, KC = 64, KC8 = KC / 8;
-constexpr int kTcThreads = 128;
-constexpr int kAResident = 256;                         // query K extent kept resident in shared memory
-constexpr int kSmemA = TM * kAResident * 2;             // 64 KiB
-constexpr int kSmemB = TN * KC * 2;                     // 32 KiB
-constexpr int kSmemDyn = kSmemA + kSmemB + 1024;        // + alignment slack; caps residency at 2 CTAs/SM
-constexpr int kChunkBytes = TM * KC * 2;                // one K chunk of the query tile
-constexpr int64_t kSampleMax = 32768;                   // sample rows per query
-constexpr int kCandCap = 8192;                          // candidates per query
-constexpr int kSelThreads = 1024;
+constexpr int TM = 128, TN = 256, KC = 64;
+constexpr int kStages = 4;
+constexpr int kStageA = TM * KC * 2;                    // 16 KiB of queries
+constexpr int kStageB = TN * KC * 2;                    // 32 KiB of rows
+constexpr int kStageBytes = kStageA + kStageB;
+constexpr int kSmemDyn = kStages * kStageBytes + 1024;  // + alignment slack: one CTA per SM
+constexpr int kTcThreads = 320;                         // producer, MMA, eight epilogue warps
+constexpr int kTmemCols = 2 * TN;                       // two accumulators
+constexpr int64_t kSampleMax = 65536;                   // sample rows per query
+constexpr int kGroup = 16;                              // sampled rows per group minimum
+constexpr int kCandCapMax = 8192;                       // candidates per query, at most
+constexpr int kSelThreads = 256;
 constexpr int kRerankThreads = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded wait on the tensor core: 2 s
 
@@ -51,11 +65,29 @@ constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN 
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Shared-memory matrix descriptor: start address, leading byte offset (between core matrices
-// along K), stride byte offset (between 8-row groups), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle layout that TMA
+// writes (8-row groups of 128-byte rows, 1024 bytes apart): start address >> 4, leading byte
+// offset 16 (unused for this layout), stride byte offset 1024, descriptor version 1 (bit 46),
+// layout type 2 = 128-byte swizzle (bits 61-63). A K step of 16 elements moves the start by 32 bytes.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void* tmap, int32_t x, int32_t y, uint32_t mbar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -160,146 +192,242 @@ __global__ void row_maxima_kernel(const float* norms, const float* resid, int64_
     }
 }
 
-// Copies rows [row0, row0 + rows) x columns [k0, k0 + KC) of a bf16 matrix (row r at
-// src + r * stride * kpad) into the core-matrix layout: core (r / 8, c / 8) at
-// ((r / 8) * KC8 + c / 8) * 128 bytes, row r % 8 of it at + (r % 8) * 16. Consecutive threads
-// write consecutive 16-byte pieces; rows beyond `valid` are zero.
-__device__ __forceinline__ void stage(uint8_t* dst, const __nv_bfloat16* __restrict__ src, int64_t row0, int64_t valid,
-                                      int64_t stride, int rows, int32_t kpad, int k0) {
-    for (int t = threadIdx.x; t < rows * KC8; t += kTcThreads) {
-        const int r8 = t & 7, kc = (t >> 3) % KC8, m8 = (t >> 3) / KC8;
-        const int64_t row = row0 + m8 * 8 + r8;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (row < valid) v = *reinterpret_cast<const uint4*>(src + row * stride * kpad + k0 + kc * 8);
-        *reinterpret_cast<uint4*>(dst + t * 16) = v;
-    }
+// 32 consecutive accumulator columns of this warp's 32 lanes (one register per column).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* v) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                   "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+                   "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                 : "r"(taddr) : "memory");
+}
+
+// (u0, u1) = (x0 - 2 v0, x1 - 2 v1) in one paired float32 FMA (each lane rounded once).
+__device__ __forceinline__ void xn_minus_2v(float x0, float x1, uint32_t v0, uint32_t v1, float& u0, float& u1) {
+    unsigned long long vv, xx, r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(vv) : "r"(v0), "r"(v1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(xx) : "f"(x0), "f"(x1));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(vv), "l"(0xC0000000C0000000ull), "l"(xx));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(u0), "=f"(u1) : "l"(r));
 }
 
 struct TcArgs {
-    const __nv_bfloat16* qb;       // [nq][kpad]
-    const float* qn;               // [nq]
-    int64_t nq;
-    const __nv_bfloat16* xb;       // rows, row c of this pass at xb + c * row_stride * kpad
-    const float* xn;               // row norms, same indexing
+    int32_t q_row0;                // first query of this chunk (tensor-map row)
+    int32_t nq;                    // queries in this chunk
+    int32_t qblocks;               // ceil(nq / 128)
     int64_t ncols;                 // rows in this pass
-    int64_t row_stride;
-    int32_t kpad;
-    float* D;                      // sample pass: [nq][ncols]
+    int64_t tiles;                 // ceil(ncols / 256)
+    int32_t nk;                    // kpad / 64
+    const float* qn;               // [nq] squared norms of this chunk's queries
+    const float* xn;               // squared norms of this pass's rows, zero-padded to tiles * 256
+    float* gmin;                   // sample pass: [nq][ceil(ncols / 16)] group minima
     const float* limit;            // filter pass: [nq]
     unsigned long long* cand;      // filter pass: [nq][cap] keys okey(a) << 32 | row
     int32_t* cnt;                  // filter pass: [nq]
     int32_t cap;
-    int32_t* error;                // set to 1 when a tensor-core wait ran out
+    int32_t* error;                // set to 1 when a wait ran out
 };
 
-// Grid: x = query tile (128 queries), y = column stripe; CTA (x, y) walks column tiles y, y + gy, ...
-// The query tile's K extent stays in shared memory when kpad <= 256, else it is staged per chunk.
 template <bool kFilter>
-__global__ void __launch_bounds__(kTcThreads, 2) dist_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_constant__ CUtensorMap tq,
+                                                               const __grid_constant__ CUtensorMap tx, const TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t tmem_base;
-    uint8_t* As = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-    uint8_t* Bs = As + kSmemA;
+    __shared__ __align__(16) float xn_tile[8][128];          // each epilogue warp's row norms
+    const uint32_t ring = smem_u32(smem_raw) + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t q0 = (int64_t)blockIdx.x * TM;
-    const uint32_t mb = smem_u32(&mbar);
-    const int nk = a.kpad / KC;
-    const bool a_resident = a.kpad <= kAResident;
+    const int64_t items = (int64_t)a.qblocks * a.tiles;
     if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full_bar[s]), 1);
+            mbar_init(smem_u32(&empty_bar[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&tfull_bar[b]), 1);
+            mbar_init(smem_u32(&tempty_bar[b]), 8);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(TN) : "memory");
+                     "r"(kTmemCols) : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    if (a_resident)
-        for (int kc = 0; kc < nk; ++kc) stage(As + kc * kChunkBytes, a.qb, q0, a.nq, 1, TM, a.kpad, kc * KC);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const int64_t qrow = q0 + warp * 32 + lane;           // the query in this thread's tensor-memory lane
-    const bool qvalid = qrow < a.nq;
-    const float qnorm = qvalid ? a.qn[qrow] : 0.f;
-    const float lim = (kFilter && qvalid) ? a.limit[qrow] : 0.f;
-    const int64_t tiles = (a.ncols + TN - 1) / TN;
-    uint32_t phase = 0;
     bool failed = false;
-    for (int64_t tile = blockIdx.y; tile < tiles && !failed; tile += gridDim.y) {
-        const int64_t x0 = tile * TN;
-        for (int kc = 0; kc < nk; ++kc) {
-            const uint8_t* Ak = a_resident ? As + kc * kChunkBytes : As;
-            if (!a_resident) stage(As, a.qb, q0, a.nq, 1, TM, a.kpad, kc * KC);
-            stage(Bs, a.xb, x0, a.ncols, a.row_stride, TN, a.kpad, kc * KC);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");      // generic writes -> tensor core
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-                for (int s = 0; s < KC / 16; ++s) {
-                    const uint64_t ad = make_desc(smem_u32(Ak) + s * 256, 128, KC8 * 128);
-                    const uint64_t bd = make_desc(smem_u32(Bs) + s * 256, 128, KC8 * 128);
-                    const uint32_t accumulate = (kc > 0 || s > 0) ? 1u : 0u;
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-                                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate) : "memory");
+    if (warp == 0) {
+        // ---- TMA producer ----
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&tq) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(&tx) : "memory");
+            int s = 0;
+            uint32_t ph = 0;
+            for (int64_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
+                const int32_t qy = a.q_row0 + (int32_t)(w % a.qblocks) * TM;
+                const int32_t xy = (int32_t)(w / a.qblocks) * TN;
+                for (int kc = 0; kc < a.nk; ++kc) {
+                    if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u)) {
+                        failed = true;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect_tx(fb, kStageBytes);
+                    const uint32_t dst = ring + s * kStageBytes;
+                    tma_load_2d(dst, &tq, kc * KC, qy, fb);
+                    tma_load_2d(dst + kStageA, &tx, kc * KC, xy, fb);
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
-                             : "memory");
             }
-            const bool ok = mbar_wait(mb, phase);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {                  // block-uniform decision
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        // ---- MMA issuer ----
+        if (lane == 0) {
+            int s = 0, acc = 0;
+            uint32_t ph = 0, aph = 0;
+            for (int64_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
+                if (!mbar_wait(smem_u32(&tempty_bar[acc]), aph ^ 1u)) {
+                    failed = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(acc * TN);
+                for (int kc = 0; kc < a.nk; ++kc) {
+                    if (!mbar_wait(smem_u32(&full_bar[s]), ph)) {
+                        failed = true;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = ring + s * kStageBytes, sb = sa + kStageA;
+#pragma unroll
+                    for (int k16 = 0; k16 < KC / 16; ++k16) {
+                        const uint64_t ad = sw128_desc(sa + k16 * 32), bd = sw128_desc(sb + k16 * 32);
+                        const uint32_t accumulate = (kc > 0 || k16 > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+                                     ::"r"(d), "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate) : "memory");
+                    }
+                    mma_commit(smem_u32(&empty_bar[s]));        // the stage is free once these MMAs finish
+                    if (++s == kStages) {
+                        s = 0;
+                        ph ^= 1u;
+                    }
+                }
+                if (failed) break;
+                mma_commit(smem_u32(&tfull_bar[acc]));          // the tile is ready for the epilogue
+                if (++acc == 2) {
+                    acc = 0;
+                    aph ^= 1u;
+                }
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue warps 2-9: tensor-memory lanes 32 * (warp % 4) ... + 31, accumulator columns
+        // 128 * ((warp - 2) / 4) ... + 127. Per column u = |x|^2 - 2 q.x (one paired FMA) and
+        // a = |q|^2 + u. The filter compares u with T = limit - |q|^2 rounded up, so a row passes
+        // whenever a <= limit; stored keys and group minima are |q|^2 + u. Both roundings are
+        // inside the error bound.
+        const int quarter = warp & 3, cgroup = (warp - 2) >> 2;
+        const float4* xs4 = reinterpret_cast<const float4*>(xn_tile[warp - 2]);
+        const int ng = (int)((a.ncols + 15) / 16);
+        int acc = 0;
+        uint32_t aph = 0;
+        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
+            const int64_t qrow = (w % a.qblocks) * TM + quarter * 32 + lane;
+            const int64_t xc = (w / a.qblocks) * TN + cgroup * 128;
+            const bool qvalid = qrow < a.nq;
+            const float4 xpre = __ldg(reinterpret_cast<const float4*>(a.xn + xc) + lane);   // norms are padded
+            const float qnorm = qvalid ? a.qn[qrow] : 0.f;
+            float T = 0.f;
+            if (kFilter && qvalid) {
+                const float d = a.limit[qrow] - qnorm;
+                T = d + fabsf(d) * 2.3841858e-07f;
+            }
+            const bool ok = mbar_wait(smem_u32(&tfull_bar[acc]), aph);
+            if (!__all_sync(0xffffffffu, ok)) {
                 failed = true;
                 break;
             }
-        }
-        if (failed) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            reinterpret_cast<float4*>(xn_tile[warp - 2])[lane] = xpre;
+            __syncwarp();
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TN + cgroup * 128);
 #pragma unroll 1
-        for (int c0 = 0; c0 < TN; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                         : "r"(taddr) : "memory");
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (!qvalid) continue;
+            for (int c = 0; c < 4; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(c * 32), v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const int64_t xg = xc + c * 32;
+                if (!qvalid || xg >= a.ncols) continue;
+                float u[32];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int64_t x = x0 + c0 + j;
-                if (x >= a.ncols) break;
-                const float d = qnorm + __ldg(a.xn + x * a.row_stride) - 2.f * __uint_as_float(v[j]);
+                for (int j4 = 0; j4 < 8; ++j4) {
+                    const float4 xv = xs4[c * 8 + j4];
+                    xn_minus_2v(xv.x, xv.y, v[j4 * 4], v[j4 * 4 + 1], u[j4 * 4], u[j4 * 4 + 1]);
+                    xn_minus_2v(xv.z, xv.w, v[j4 * 4 + 2], v[j4 * 4 + 3], u[j4 * 4 + 2], u[j4 * 4 + 3]);
+                }
+                if (xg + 32 > a.ncols) {                        // zero-filled rows past the end: NaN never
+#pragma unroll                                                  // compares <= and fminf skips it
+                    for (int j = 0; j < 32; ++j)
+                        if (xg + j >= a.ncols) u[j] = __int_as_float(0x7fc00000);
+                }
+                float m[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) m[j] = fminf(u[j], u[j + 16]);   // tree: m[j] covers j, j+16
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m[j] = fminf(m[j], m[j + 8]);
                 if (kFilter) {
-                    if (d <= lim) {
-                        const int p = atomicAdd(a.cnt + qrow, 1);
-                        if (p < a.cap) a.cand[qrow * a.cap + p] = ((unsigned long long)okey(d) << 32) | (uint32_t)x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) m[j] = fminf(m[j], m[j + 4]);
+                    if (fminf(fminf(m[0], m[1]), fminf(m[2], m[3])) <= T) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) {
+                            if (u[j] <= T && xg + j < a.ncols) {
+                                const int p = atomicAdd(a.cnt + qrow, 1);
+                                if (p < a.cap)
+                                    a.cand[qrow * a.cap + p] = ((unsigned long long)okey(qnorm + u[j]) << 32) | (uint32_t)(xg + j);
+                            }
+                        }
                     }
                 } else {
-                    a.D[qrow * a.ncols + x] = d;
+                    // group minima need rows j..j+15 together: redo the last levels on halves
+                    float g0 = u[0], g1 = u[16];
+#pragma unroll
+                    for (int j = 1; j < 16; ++j) {
+                        g0 = fminf(g0, u[j]);
+                        g1 = fminf(g1, u[16 + j]);
+                    }
+                    a.gmin[qrow * ng + xg / 16] = qnorm + g0;
+                    if (xg + 16 < a.ncols) a.gmin[qrow * ng + xg / 16 + 1] = qnorm + g1;
                 }
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
+            if (++acc == 2) {
+                acc = 0;
+                aph ^= 1u;
+            }
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
     }
-    if (failed) {
-        // the last commit may still be outstanding: wait for it once more (bounded), then free
-        const bool ok = mbar_wait(mb, phase ^ 1u);
-        (void)ok;
-        if (threadIdx.x == 0) atomicExch(a.error, 1);
-    }
+    if (failed && lane == 0) atomicExch(a.error, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
 // Radix select over `count` 32-bit keys: the key of rank `rank` (0-based), keys read through
-// get(i); four passes of 8-bit digits.
+// get(i); four passes of 8-bit digits. Lanes of a warp that hit the same bin add once (keys of
+// one query crowd into a few bins).
 template <int kThreads, typename Get>
 __device__ uint32_t radix_select32(int count, uint32_t rank, Get get, uint32_t* hist, uint32_t* prefix_s, uint32_t* rank_s) {
     if (threadIdx.x == 0) {
@@ -312,9 +440,15 @@ __device__ uint32_t radix_select32(int count, uint32_t rank, Get get, uint32_t* 
         const int shift = 24 - 8 * pass;
         const uint32_t want = *prefix_s;
         const uint32_t hmask = pass == 0 ? 0u : (0xffffffffu << (shift + 8));
-        for (int i = threadIdx.x; i < count; i += kThreads) {
-            const uint32_t kv = get(i);
-            if ((kv & hmask) == (want & hmask)) atomicAdd(&hist[(kv >> shift) & 0xffu], 1u);
+        for (int i0 = 0; i0 < count; i0 += kThreads) {
+            const int i = i0 + (int)threadIdx.x;
+            uint32_t bin = 256u;
+            if (i < count) {
+                const uint32_t kv = get(i);
+                if ((kv & hmask) == (want & hmask)) bin = (kv >> shift) & 0xffu;
+            }
+            const uint32_t peers = __match_any_sync(0xffffffffu, bin);
+            if (bin < 256u && (threadIdx.x & 31) == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -332,24 +466,29 @@ __device__ uint32_t radix_select32(int count, uint32_t rank, Get get, uint32_t* 
     return *prefix_s;
 }
 
-// limit[q] = window_limit(k-th smallest sampled a, b_q). Dynamic shared memory: ns keys.
-__global__ void __launch_bounds__(kSelThreads) sample_limit_kernel(const float* __restrict__ Ds, int64_t ns, int k,
+// limit[q] = window_limit(k-th smallest group minimum, b_q); +inf when there are fewer than k
+// groups (every row is then a candidate).
+__global__ void __launch_bounds__(kSelThreads) sample_limit_kernel(const float* __restrict__ gmin, int ng, int k,
                                                                   const float* __restrict__ qn, const float* __restrict__ rq,
                                                                   const float* __restrict__ maxima, int32_t kpad,
                                                                   float* __restrict__ limit) {
-    extern __shared__ uint32_t skeys[];
+    __shared__ uint32_t skeys[kSampleMax / kGroup];
     __shared__ uint32_t hist[256], prefix_s, rank_s;
     const int64_t q = blockIdx.x;
-    for (int64_t i = threadIdx.x; i < ns; i += kSelThreads) skeys[i] = okey(Ds[q * ns + i]);
+    if (ng < k) {
+        if (threadIdx.x == 0) limit[q] = __int_as_float(0x7f800000);
+        return;
+    }
+    for (int i = threadIdx.x; i < ng; i += kSelThreads) skeys[i] = okey(gmin[q * ng + i]);
     __syncthreads();
-    const uint32_t tk = radix_select32<kSelThreads>((int)ns, (uint32_t)(k - 1), [&](int i) { return skeys[i]; }, hist,
+    const uint32_t tk = radix_select32<kSelThreads>(ng, (uint32_t)(k - 1), [&](int i) { return skeys[i]; }, hist,
                                                     &prefix_s, &rank_s);
     if (threadIdx.x == 0) limit[q] = window_limit(from_okey(tk), error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
 }
 
-// Re-rank (step 4). Dynamic shared memory: two arrays of kCandCap 64-bit keys.
+// Re-rank (step 4). Dynamic shared memory: two arrays of `cap` 64-bit keys (cap a power of 2).
 __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned long long* __restrict__ cand,
-                                                               const int32_t* __restrict__ cnt, int k,
+                                                               const int32_t* __restrict__ cnt, int cap, int k,
                                                                const float* __restrict__ qf, const float* __restrict__ xf,
                                                                int32_t dim, const float* __restrict__ qn,
                                                                const float* __restrict__ rq, const float* __restrict__ maxima,
@@ -357,16 +496,16 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned l
                                                                float* __restrict__ dists, int32_t* __restrict__ ov) {
     extern __shared__ unsigned long long rk[];
     unsigned long long* keys = rk;
-    unsigned long long* sel = rk + kCandCap;
+    unsigned long long* sel = rk + cap;
     __shared__ uint32_t hist[256], prefix_s, rank_s;
     __shared__ int m_s;
     const int64_t q = blockIdx.x;
     const int c = cnt[q];
-    if (c > kCandCap) {                                  // recomputed by the CUDA-core path
+    if (c > cap) {                                       // recomputed by the CUDA-core path
         if (threadIdx.x == 0) ov[1 + atomicAdd(ov, 1)] = (int32_t)q;
         return;
     }
-    for (int i = threadIdx.x; i < c; i += kRerankThreads) keys[i] = cand[q * kCandCap + i];
+    for (int i = threadIdx.x; i < c; i += kRerankThreads) keys[i] = cand[q * cap + i];
     if (threadIdx.x == 0) m_s = 0;
     __syncthreads();
     const uint32_t tk = radix_select32<kRerankThreads>(c, (uint32_t)(k - 1), [&](int i) { return (uint32_t)(keys[i] >> 32); },
@@ -428,8 +567,46 @@ __global__ void scatter_results_kernel(const int32_t* __restrict__ gid, const fl
     }
 }
 
+// xs[j] = xn[j * stride] for j < ns; zero up to `padded`.
+__global__ void strided_norms_kernel(const float* __restrict__ xn, int64_t stride, int64_t ns, int64_t padded,
+                                     float* __restrict__ xs) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < padded; j += (int64_t)gridDim.x * blockDim.x)
+        xs[j] = j < ns ? xn[j * stride] : 0.f;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                                   const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no link to libcuda).
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// 2-D bf16 map over `rows` rows of `kpad` elements, `row_bytes` apart; box 64 x box_rows with the
+// 128-byte swizzle; rows past the end read as zero.
+bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kpad, uint64_t row_bytes, uint32_t box_rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {kpad, rows};
+    const cuuint64_t strides[1] = {row_bytes};
+    const cuuint32_t box[2] = {(cuuint32_t)KC, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct Scratch {
-    void* p[12] = {};
+    void* p[13] = {};
     ~Scratch() {
         for (void* q : p) cudaFree(q);
     }
@@ -445,12 +622,18 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     const int32_t kpad = (dim + KC - 1) / KC * KC;
     const int64_t stride = (n + kSampleMax - 1) / kSampleMax;
     const int64_t ns = (n + stride - 1) / stride;
+    const int64_t ng = (ns + kGroup - 1) / kGroup;
     const int64_t chunk = std::min<int64_t>((nq + TM - 1) / TM * TM, 16384);
+    // about k * stride rows fall below the sampled threshold; room for four times that
+    int cap = 2048;
+    while (cap < kCandCapMax && (int64_t)cap < 8 * (int64_t)k * stride) cap <<= 1;
+    const int64_t tiles_n = (n + TN - 1) / TN, tiles_s = (ns + TN - 1) / TN;
     Scratch s;
     cudaError_t e = cudaSuccess;
-    const size_t sizes[] = {2ull * n * kpad, 4ull * n, 4ull * n, 2ull * nq * kpad, 4ull * nq, 4ull * nq, 16,
-                            4ull * chunk * ns, 4ull * chunk, 8ull * chunk * kCandCap, 4ull * chunk, 4ull * (chunk + 2)};
-    for (int i = 0; i < 12 && e == cudaSuccess; ++i) e = cudaMalloc(&s.p[i], std::max<size_t>(sizes[i], 16));
+    const size_t sizes[] = {2ull * n * kpad, 4ull * tiles_n * TN, 4ull * n, 2ull * nq * kpad, 4ull * nq, 4ull * nq, 16,
+                            4ull * chunk * ng, 4ull * chunk, 8ull * chunk * cap, 4ull * chunk, 4ull * (chunk + 2),
+                            4ull * tiles_s * TN};
+    for (int i = 0; i < 13 && e == cudaSuccess; ++i) e = cudaMalloc(&s.p[i], std::max<size_t>(sizes[i], 16));
     if (e != cudaSuccess) return *why = std::string("knn scratch: ") + cudaGetErrorString(e), (int)e;
     auto* xb = static_cast<__nv_bfloat16*>(s.p[0]);
     auto* xn = static_cast<float*>(s.p[1]);
@@ -459,40 +642,43 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     auto* qn = static_cast<float*>(s.p[4]);
     auto* qr = static_cast<float*>(s.p[5]);
     auto* maxima = static_cast<float*>(s.p[6]);
-    auto* Ds = static_cast<float*>(s.p[7]);
+    auto* gmin = static_cast<float*>(s.p[7]);
     auto* limit = static_cast<float*>(s.p[8]);
     auto* cand = static_cast<unsigned long long*>(s.p[9]);
     auto* cnt = static_cast<int32_t*>(s.p[10]);
     auto* ov = static_cast<int32_t*>(s.p[11]);         // [0] overflow count, [1..chunk] queries, [chunk+1] error
+    auto* xs = static_cast<float*>(s.p[12]);
     int32_t* err = ov + chunk + 1;
-    const int sample_smem = (int)(4 * ns), rerank_smem = 2 * kCandCap * 8;
+    const int rerank_smem = 2 * cap * 8;
     if ((e = cudaFuncSetAttribute(dist_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(dist_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(sample_limit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sample_smem)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rerank_smem)) != cudaSuccess)
         return *why = cudaGetErrorString(e), (int)e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    CUtensorMap tq, tx_all, tx_sample;
+    if (!make_map(&tq, qb, nq, kpad, 2ull * kpad, TM) || !make_map(&tx_all, xb, n, kpad, 2ull * kpad, TN) ||
+        !make_map(&tx_sample, xb, ns, kpad, 2ull * kpad * stride, TN))
+        return *why = "tensor map encoding failed", (int)cudaErrorInvalidValue;
     cudaMemsetAsync(maxima, 0, 16, st);
+    cudaMemsetAsync(xn, 0, 4ull * tiles_n * TN, st);
     bf16_rows_kernel<<<2048, 256, 0, st>>>(base, n, dim, kpad, xb, xn, xr);
     bf16_rows_kernel<<<1024, 256, 0, st>>>(queries, nq, dim, kpad, qb, qn, qr);
     row_maxima_kernel<<<304, 256, 0, st>>>(xn, xr, n, maxima);
+    strided_norms_kernel<<<256, 256, 0, st>>>(xn, stride, ns, tiles_s * TN, xs);
     for (int64_t q0 = 0; q0 < nq && e == cudaSuccess; q0 += chunk) {
         const int64_t qc = std::min(chunk, nq - q0);
-        const int64_t qblocks = (qc + TM - 1) / TM;
-        auto stripes = [&](int64_t cols) {
-            const int64_t tiles = (cols + TN - 1) / TN;
-            return (unsigned)std::max<int64_t>(1, std::min<int64_t>(tiles, (2ll * sms) / qblocks));
-        };
-        const TcArgs sa{qb + q0 * kpad, qn + q0, qc, xb, xn, ns, stride, kpad, Ds, nullptr, nullptr, nullptr, 0, err};
-        const TcArgs fa{qb + q0 * kpad, qn + q0, qc, xb, xn, n, 1, kpad, nullptr, limit, cand, cnt, kCandCap, err};
+        const int32_t qblocks = (int32_t)((qc + TM - 1) / TM);
+        auto grid = [&](int64_t tiles) { return (unsigned)std::min<int64_t>((int64_t)qblocks * tiles, sms); };
+        const TcArgs sa{(int32_t)q0, (int32_t)qc, qblocks, ns, tiles_s, kpad / KC, qn + q0, xs, gmin, nullptr, nullptr, nullptr, 0, err};
+        const TcArgs fa{(int32_t)q0, (int32_t)qc, qblocks, n, tiles_n, kpad / KC, qn + q0, xn, nullptr, limit, cand, cnt, cap, err};
         cudaMemsetAsync(ov, 0, 4ull * (chunk + 2), st);
         cudaMemsetAsync(cnt, 0, 4ull * qc, st);
-        dist_tc_kernel<false><<<dim3((unsigned)qblocks, stripes(ns)), kTcThreads, kSmemDyn, st>>>(sa);
-        sample_limit_kernel<<<(unsigned)qc, kSelThreads, sample_smem, st>>>(Ds, ns, k, qn + q0, qr + q0, maxima, kpad, limit);
-        dist_tc_kernel<true><<<dim3((unsigned)qblocks, stripes(n)), kTcThreads, kSmemDyn, st>>>(fa);
-        rerank_kernel<<<(unsigned)qc, kRerankThreads, rerank_smem, st>>>(cand, cnt, k, queries + q0 * dim, base, dim, qn + q0,
+        dist_tc_kernel<false><<<grid(tiles_s), kTcThreads, kSmemDyn, st>>>(tq, tx_sample, sa);
+        sample_limit_kernel<<<(unsigned)qc, kSelThreads, 0, st>>>(gmin, (int)ng, k, qn + q0, qr + q0, maxima, kpad, limit);
+        dist_tc_kernel<true><<<grid(tiles_n), kTcThreads, kSmemDyn, st>>>(tq, tx_all, fa);
+        rerank_kernel<<<(unsigned)qc, kRerankThreads, rerank_smem, st>>>(cand, cnt, cap, k, queries + q0 * dim, base, dim, qn + q0,
                                                                         qr + q0, maxima, kpad, ids + q0 * k, dists + q0 * k, ov);
         int32_t flags[2] = {0, 0};
         if ((e = cudaGetLastError()) != cudaSuccess) break;

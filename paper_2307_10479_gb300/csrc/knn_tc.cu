@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
     __shared__ __align__(16) float xn_tile[8][128];          // each epilogue warp's row norms
     const uint32_t ring = smem_u32(smem_raw) + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t items = (int64_t)a.qblocks * a.tiles;
+    const uint32_t items = (uint32_t)(a.qblocks * a.tiles);      // < 2^31: checked by the caller
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&full_bar[s]), 1);
@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
             asm volatile("prefetch.tensormap [%0];" ::"l"(&tx) : "memory");
             int s = 0;
             uint32_t ph = 0;
-            for (int64_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
-                const int32_t qy = a.q_row0 + (int32_t)(w % a.qblocks) * TM;
-                const int32_t xy = (int32_t)(w / a.qblocks) * TN;
+            for (uint32_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
+                const int32_t qy = a.q_row0 + (int32_t)(w % (uint32_t)a.qblocks) * TM;
+                const int32_t xy = (int32_t)(w / (uint32_t)a.qblocks) * TN;
                 for (int kc = 0; kc < a.nk; ++kc) {
                     if (!mbar_wait(smem_u32(&empty_bar[s]), ph ^ 1u)) {
                         failed = true;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         if (lane == 0) {
             int s = 0, acc = 0;
             uint32_t ph = 0, aph = 0;
-            for (int64_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
+            for (uint32_t w = blockIdx.x; w < items && !failed; w += gridDim.x) {
                 if (!mbar_wait(smem_u32(&tempty_bar[acc]), aph ^ 1u)) {
                     failed = true;
                     break;
@@ -341,9 +341,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         const int ng = (int)((a.ncols + 15) / 16);
         int acc = 0;
         uint32_t aph = 0;
-        for (int64_t w = blockIdx.x; w < items; w += gridDim.x) {
-            const int64_t qrow = (w % a.qblocks) * TM + quarter * 32 + lane;
-            const int64_t xc = (w / a.qblocks) * TN + cgroup * 128;
+        for (uint32_t w = blockIdx.x; w < items; w += gridDim.x) {
+            const int64_t qrow = (int64_t)(w % (uint32_t)a.qblocks) * TM + quarter * 32 + lane;
+            const int64_t xc = (int64_t)(w / (uint32_t)a.qblocks) * TN + cgroup * 128;
             const bool qvalid = qrow < a.nq;
             const float4 xpre = __ldg(reinterpret_cast<const float4*>(a.xn + xc) + lane);   // norms are padded
             const float qnorm = qvalid ? a.qn[qrow] : 0.f;
@@ -486,7 +486,8 @@ __global__ void __launch_bounds__(kSelThreads) sample_limit_kernel(const float* 
     if (threadIdx.x == 0) limit[q] = window_limit(from_okey(tk), error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
 }
 
-// Re-rank (step 4). Dynamic shared memory: two arrays of `cap` 64-bit keys (cap a power of 2).
+// Re-rank (step 4). Dynamic shared memory: two arrays of `cap` 64-bit keys (cap a power of 2) and
+// the query row.
 __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned long long* __restrict__ cand,
                                                                const int32_t* __restrict__ cnt, int cap, int k,
                                                                const float* __restrict__ qf, const float* __restrict__ xf,
@@ -497,6 +498,7 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned l
     extern __shared__ unsigned long long rk[];
     unsigned long long* keys = rk;
     unsigned long long* sel = rk + cap;
+    float* qv = reinterpret_cast<float*>(rk + 2 * cap);
     __shared__ uint32_t hist[256], prefix_s, rank_s;
     __shared__ int m_s;
     const int64_t q = blockIdx.x;
@@ -506,21 +508,35 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned l
         return;
     }
     for (int i = threadIdx.x; i < c; i += kRerankThreads) keys[i] = cand[q * cap + i];
+    for (int j = threadIdx.x; j < dim; j += kRerankThreads) qv[j] = qf[q * dim + j];
     if (threadIdx.x == 0) m_s = 0;
     __syncthreads();
     const uint32_t tk = radix_select32<kRerankThreads>(c, (uint32_t)(k - 1), [&](int i) { return (uint32_t)(keys[i] >> 32); },
                                                        hist, &prefix_s, &rank_s);
     const float lim = window_limit(from_okey(tk), error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
-    const float* qv = qf + q * dim;
+    const bool vec = (dim & 3) == 0 && (reinterpret_cast<uintptr_t>(xf) & 15) == 0;
     for (int i = threadIdx.x; i < c; i += kRerankThreads) {
         const unsigned long long key = keys[i];
         if (from_okey((uint32_t)(key >> 32)) > lim) continue;
         const uint32_t x = (uint32_t)key;
         const float* xv = xf + (int64_t)x * dim;
         float e = 0.f;
-        for (int j = 0; j < dim; ++j) {                  // dimension order, as the CUDA-core path
-            const float u = qv[j] - xv[j];
-            e = fmaf(u, u, e);
+        int j = 0;                                       // dimension order, as the CUDA-core path
+        if (vec)
+            for (; j < dim; j += 4) {
+                const float4 r = __ldg(reinterpret_cast<const float4*>(xv + j));
+                float t = qv[j] - r.x;
+                e = fmaf(t, t, e);
+                t = qv[j + 1] - r.y;
+                e = fmaf(t, t, e);
+                t = qv[j + 2] - r.z;
+                e = fmaf(t, t, e);
+                t = qv[j + 3] - r.w;
+                e = fmaf(t, t, e);
+            }
+        for (; j < dim; ++j) {
+            const float t = qv[j] - xv[j];
+            e = fmaf(t, t, e);
         }
         sel[atomicAdd(&m_s, 1)] = ((unsigned long long)__float_as_uint(e) << 32) | x;
     }
@@ -619,14 +635,15 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (k > n) return *why = "k larger than n", (int)cudaErrorInvalidValue;
     if (nq == 0) return 0;
+    if (n > INT32_MAX - TN) return *why = "n too large", (int)cudaErrorInvalidValue;   // work items fit 31 bits
     const int32_t kpad = (dim + KC - 1) / KC * KC;
     const int64_t stride = (n + kSampleMax - 1) / kSampleMax;
     const int64_t ns = (n + stride - 1) / stride;
     const int64_t ng = (ns + kGroup - 1) / kGroup;
     const int64_t chunk = std::min<int64_t>((nq + TM - 1) / TM * TM, 16384);
-    // about k * stride rows fall below the sampled threshold; room for four times that
-    int cap = 2048;
-    while (cap < kCandCapMax && (int64_t)cap < 8 * (int64_t)k * stride) cap <<= 1;
+    // about k * stride rows fall below the sampled threshold; room for twice that
+    int cap = 1024;
+    while (cap < kCandCapMax && (int64_t)cap < 2 * (int64_t)k * stride) cap <<= 1;
     const int64_t tiles_n = (n + TN - 1) / TN, tiles_s = (ns + TN - 1) / TN;
     Scratch s;
     cudaError_t e = cudaSuccess;
@@ -649,7 +666,7 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     auto* ov = static_cast<int32_t*>(s.p[11]);         // [0] overflow count, [1..chunk] queries, [chunk+1] error
     auto* xs = static_cast<float*>(s.p[12]);
     int32_t* err = ov + chunk + 1;
-    const int rerank_smem = 2 * cap * 8;
+    const int rerank_smem = 2 * cap * 8 + 4 * ((dim + 1) & ~1);
     if ((e = cudaFuncSetAttribute(dist_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(dist_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
         (e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rerank_smem)) != cudaSuccess)

@@ -91,6 +91,8 @@ void free_device(deg_index* idx) {
     cudaFree(d.old2new);
     cudaFree(d.new2old);
     cudaFree(d.pivots);
+    knn_plan_destroy(d.route_plan);
+    d.route_plan = nullptr;
     cudaFree(d.stop_w);
     d = DeviceIndex{};
     workspace_free(idx->ws);

@@ -44,6 +44,7 @@ struct DeviceIndex {
     int32_t entry_internal = -1;
     int32_t* pivots = nullptr;    // [npivots] internal ids of the layout's pivots
     int32_t npivots = 0;
+    struct KnnPlan* route_plan = nullptr;   // nearest-pivot search over the pivots' rows (knn_tc.cu)
     uint16_t* stop_w = nullptr;   // learned-stop weights, bfloat16, inference layout (mlp.cu)
     float stop_logit = 0.f;       // stop when logit(stop) - logit(continue) > this
 };
@@ -148,6 +149,15 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
 // The same result from CUDA-core float32 distances and a full radix select (knn_exact.cu).
 int launch_knn_simt(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
                     int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);
+// k-NN over a small fixed row set (at most 4096 rows), tensor-core distances with the exact re-rank,
+// no host synchronisation per call (knn_tc.cu). Rows are gathered at creation:
+// row i = rows[(row_ids ? row_ids[i] : i) * row_stride ...]. ids[q][0..k) are row indices.
+struct KnnPlan;
+int knn_plan_create(KnnPlan** out, const float* rows, int64_t row_stride, const int32_t* row_ids, int64_t n, int32_t dim,
+                    int32_t k, int32_t cap, deg_stream_t stream, std::string* why);
+int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, float* dists, deg_stream_t stream,
+                 std::string* why);
+void knn_plan_destroy(KnnPlan* p);
 // Same, on a fixed statically allocated scratch (no allocation in the call).
 int launch_knn_exact_noalloc(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim,
                              int32_t k, int32_t* ids, float* dists, deg_stream_t stream, std::string* why);

@@ -55,6 +55,7 @@ constexpr int kTmemCols = 2 * TN;                       // two accumulators
 constexpr int64_t kSampleMax = 65536;                   // sample rows per query
 constexpr int kGroup = 16;                              // sampled rows per group minimum
 constexpr int kCandCapMax = 8192;                       // candidates per query, at most
+constexpr int64_t kPlanRowsMax = 4096;                  // rows of a k-NN plan (inline fallback in shared memory)
 constexpr int kSelThreads = 256;
 constexpr int kRerankThreads = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bounded wait on the tensor core: 2 s
@@ -486,58 +487,118 @@ __global__ void __launch_bounds__(kSelThreads) sample_limit_kernel(const float* 
     if (threadIdx.x == 0) limit[q] = window_limit(from_okey(tk), error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
 }
 
-// Re-rank (step 4). Dynamic shared memory: two arrays of `cap` 64-bit keys (cap a power of 2) and
-// the query row.
-__global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned long long* __restrict__ cand,
-                                                               const int32_t* __restrict__ cnt, int cap, int k,
-                                                               const float* __restrict__ qf, const float* __restrict__ xf,
-                                                               int32_t dim, const float* __restrict__ qn,
-                                                               const float* __restrict__ rq, const float* __restrict__ maxima,
-                                                               int32_t kpad, int32_t* __restrict__ ids,
-                                                               float* __restrict__ dists, int32_t* __restrict__ ov) {
-    extern __shared__ unsigned long long rk[];
-    unsigned long long* keys = rk;
-    unsigned long long* sel = rk + cap;
-    float* qv = reinterpret_cast<float*>(rk + 2 * cap);
+// Exact float32 squared distance of row x, summed in dimension order (as the CUDA-core path).
+__device__ __forceinline__ float exact_row_d2(const float* qv, const float* __restrict__ xf, int64_t x, int32_t dim, bool vec) {
+    const float* xv = xf + x * dim;
+    float e = 0.f;
+    int j = 0;
+    if (vec)
+        for (; j < dim; j += 4) {
+            const float4 r = __ldg(reinterpret_cast<const float4*>(xv + j));
+            float t = qv[j] - r.x;
+            e = fmaf(t, t, e);
+            t = qv[j + 1] - r.y;
+            e = fmaf(t, t, e);
+            t = qv[j + 2] - r.z;
+            e = fmaf(t, t, e);
+            t = qv[j + 3] - r.w;
+            e = fmaf(t, t, e);
+        }
+    for (; j < dim; ++j) {
+        const float t = qv[j] - xv[j];
+        e = fmaf(t, t, e);
+    }
+    return e;
+}
+
+// Ascending block-wide bitonic sort of P keys (P a power of two) in shared memory.
+template <int kThreads>
+__device__ void bitonic_sort(unsigned long long* a, int P) {
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride; stride >>= 1) {
+            for (int t = threadIdx.x; t < P / 2; t += kThreads) {
+                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const unsigned long long u = a[lo], w = a[hi];
+                if ((u > w) == up) {
+                    a[lo] = w;
+                    a[hi] = u;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+struct RerankArgs {
+    const unsigned long long* cand;   // [nq][cap] candidate keys okey(a) << 32 | row
+    const int32_t* cnt;               // [nq]
+    int32_t cap, k;
+    const float* qf;                  // [nq][dim] float32 queries
+    const float* xf;                  // [rows][dim] float32 rows
+    int32_t dim;
+    const float* qn;                  // [nq]
+    const float* rq;                  // [nq]
+    const float* maxima;              // [2]
+    int32_t kpad;
+    int32_t* ids;                     // [nq][k]
+    float* dists;                     // [nq][k]
+    int32_t* ov;                      // [0] count, [1..] queries left for the CUDA-core path
+    int32_t inline_n;                 // > 0: such a query is finished here, exactly, over all inline_n rows
+    const int32_t* error;             // nonzero: a tensor-core wait ran out; the results are ids -1
+};
+
+// Re-rank (step 4). Dynamic shared memory: the query row, then two arrays of `cap` 64-bit keys
+// (cap a power of 2), or, for the inline fallback, the keys of all rows.
+__global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const RerankArgs A) {
+    extern __shared__ __align__(16) unsigned long long rk[];
+    const int dim4 = (A.dim + 3) & ~3;
+    float* qv = reinterpret_cast<float*>(rk);
+    unsigned long long* keys = rk + dim4 / 2;
+    unsigned long long* sel = keys + A.cap;
     __shared__ uint32_t hist[256], prefix_s, rank_s;
     __shared__ int m_s;
     const int64_t q = blockIdx.x;
-    const int c = cnt[q];
-    if (c > cap) {                                       // recomputed by the CUDA-core path
-        if (threadIdx.x == 0) ov[1 + atomicAdd(ov, 1)] = (int32_t)q;
+    const int k = A.k;
+    if (A.error && *A.error) {
+        for (int i = threadIdx.x; i < k; i += kRerankThreads) {
+            A.ids[q * k + i] = -1;
+            A.dists[q * k + i] = __int_as_float(0x7f800000);
+        }
         return;
     }
-    for (int i = threadIdx.x; i < c; i += kRerankThreads) keys[i] = cand[q * cap + i];
-    for (int j = threadIdx.x; j < dim; j += kRerankThreads) qv[j] = qf[q * dim + j];
+    const int c = A.cnt[q];
+    if (c > A.cap && A.inline_n == 0) {                  // recomputed by the CUDA-core path
+        if (threadIdx.x == 0) A.ov[1 + atomicAdd(A.ov, 1)] = (int32_t)q;
+        return;
+    }
+    for (int j = threadIdx.x; j < A.dim; j += kRerankThreads) qv[j] = A.qf[q * A.dim + j];
+    const bool vec = (A.dim & 3) == 0 && (reinterpret_cast<uintptr_t>(A.xf) & 15) == 0;
+    if (c > A.cap) {                                     // every row, exactly
+        __syncthreads();
+        int P = 1;
+        while (P < A.inline_n) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += kRerankThreads)
+            keys[i] = i < A.inline_n ? ((unsigned long long)__float_as_uint(exact_row_d2(qv, A.xf, i, A.dim, vec)) << 32) | (uint32_t)i
+                                     : ~0ull;
+        __syncthreads();
+        bitonic_sort<kRerankThreads>(keys, P);
+        for (int i = threadIdx.x; i < k; i += kRerankThreads) {
+            A.ids[q * k + i] = (int32_t)(uint32_t)keys[i];
+            A.dists[q * k + i] = sqrtf(__uint_as_float((uint32_t)(keys[i] >> 32)));
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < c; i += kRerankThreads) keys[i] = A.cand[q * A.cap + i];
     if (threadIdx.x == 0) m_s = 0;
     __syncthreads();
     const uint32_t tk = radix_select32<kRerankThreads>(c, (uint32_t)(k - 1), [&](int i) { return (uint32_t)(keys[i] >> 32); },
                                                        hist, &prefix_s, &rank_s);
-    const float lim = window_limit(from_okey(tk), error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
-    const bool vec = (dim & 3) == 0 && (reinterpret_cast<uintptr_t>(xf) & 15) == 0;
+    const float lim = window_limit(from_okey(tk), error_bound(A.qn[q], A.rq[q], A.maxima[0], A.maxima[1], A.kpad));
     for (int i = threadIdx.x; i < c; i += kRerankThreads) {
         const unsigned long long key = keys[i];
         if (from_okey((uint32_t)(key >> 32)) > lim) continue;
         const uint32_t x = (uint32_t)key;
-        const float* xv = xf + (int64_t)x * dim;
-        float e = 0.f;
-        int j = 0;                                       // dimension order, as the CUDA-core path
-        if (vec)
-            for (; j < dim; j += 4) {
-                const float4 r = __ldg(reinterpret_cast<const float4*>(xv + j));
-                float t = qv[j] - r.x;
-                e = fmaf(t, t, e);
-                t = qv[j + 1] - r.y;
-                e = fmaf(t, t, e);
-                t = qv[j + 2] - r.z;
-                e = fmaf(t, t, e);
-                t = qv[j + 3] - r.w;
-                e = fmaf(t, t, e);
-            }
-        for (; j < dim; ++j) {
-            const float t = qv[j] - xv[j];
-            e = fmaf(t, t, e);
-        }
+        const float e = exact_row_d2(qv, A.xf, x, A.dim, vec);
         sel[atomicAdd(&m_s, 1)] = ((unsigned long long)__float_as_uint(e) << 32) | x;
     }
     __syncthreads();
@@ -546,23 +607,18 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const unsigned l
     while (P < m) P <<= 1;
     for (int i = m + threadIdx.x; i < P; i += kRerankThreads) sel[i] = ~0ull;
     __syncthreads();
-    for (int size = 2; size <= P; size <<= 1)
-        for (int stride = size >> 1; stride; stride >>= 1) {
-            for (int t = threadIdx.x; t < P / 2; t += kRerankThreads) {
-                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const unsigned long long u = sel[lo], w = sel[hi];
-                if ((u > w) == up) {
-                    sel[lo] = w;
-                    sel[hi] = u;
-                }
-            }
-            __syncthreads();
-        }
+    bitonic_sort<kRerankThreads>(sel, P);
     for (int i = threadIdx.x; i < k; i += kRerankThreads) {
-        ids[q * k + i] = (int32_t)(uint32_t)sel[i];
-        dists[q * k + i] = sqrtf(__uint_as_float((uint32_t)(sel[i] >> 32)));
+        A.ids[q * k + i] = (int32_t)(uint32_t)sel[i];
+        A.dists[q * k + i] = sqrtf(__uint_as_float((uint32_t)(sel[i] >> 32)));
     }
+}
+
+// Smem bytes of rerank_kernel.
+int rerank_smem_bytes(int cap, int dim, int inline_n) {
+    int P = 1;
+    while (P < inline_n) P <<= 1;
+    return 4 * ((dim + 3) & ~3) + 8 * std::max(2 * cap, inline_n > 0 ? P : 0);
 }
 
 __global__ void gather_rows_kernel(const float* __restrict__ src, const int32_t* __restrict__ list, int count, int32_t dim,
@@ -621,6 +677,35 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t rows, uint64_t kpad, ui
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// dst[i][0 .. dim) = src[(ids ? ids[i] : i) * stride + 0 .. dim)
+__global__ void gather_plan_rows_kernel(const float* __restrict__ src, int64_t stride, const int32_t* __restrict__ ids,
+                                        int64_t n, int32_t dim, float* __restrict__ dst) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n * dim; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = t / dim;
+        dst[t] = src[(ids ? (int64_t)ids[i] : i) * stride + t % dim];
+    }
+}
+
+// The dynamic shared-memory limit is one process-wide setting per kernel: raise it, once, to the
+// device's opt-in maximum (occupancy follows the bytes each launch asks for, not this limit).
+template <typename F>
+cudaError_t open_smem_limit(F* f, int optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, f);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
+cudaError_t open_smem_limits() {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = open_smem_limit(dist_tc_kernel<false>, optin);
+    if (e == cudaSuccess) e = open_smem_limit(dist_tc_kernel<true>, optin);
+    if (e == cudaSuccess) e = open_smem_limit(rerank_kernel, optin);
+    return e;
+}
+
 struct Scratch {
     void* p[13] = {};
     ~Scratch() {
@@ -666,11 +751,8 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     auto* ov = static_cast<int32_t*>(s.p[11]);         // [0] overflow count, [1..chunk] queries, [chunk+1] error
     auto* xs = static_cast<float*>(s.p[12]);
     int32_t* err = ov + chunk + 1;
-    const int rerank_smem = 2 * cap * 8 + 4 * ((dim + 1) & ~1);
-    if ((e = cudaFuncSetAttribute(dist_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(dist_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(rerank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, rerank_smem)) != cudaSuccess)
-        return *why = cudaGetErrorString(e), (int)e;
+    const int rerank_smem = rerank_smem_bytes(cap, dim, 0);
+    if ((e = open_smem_limits()) != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -695,8 +777,9 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
         dist_tc_kernel<false><<<grid(tiles_s), kTcThreads, kSmemDyn, st>>>(tq, tx_sample, sa);
         sample_limit_kernel<<<(unsigned)qc, kSelThreads, 0, st>>>(gmin, (int)ng, k, qn + q0, qr + q0, maxima, kpad, limit);
         dist_tc_kernel<true><<<grid(tiles_n), kTcThreads, kSmemDyn, st>>>(tq, tx_all, fa);
-        rerank_kernel<<<(unsigned)qc, kRerankThreads, rerank_smem, st>>>(cand, cnt, cap, k, queries + q0 * dim, base, dim, qn + q0,
-                                                                        qr + q0, maxima, kpad, ids + q0 * k, dists + q0 * k, ov);
+        const RerankArgs ra{cand, cnt, cap, k, queries + q0 * dim, base, dim, qn + q0, qr + q0, maxima, kpad,
+                            ids + q0 * k, dists + q0 * k, ov, 0, nullptr};
+        rerank_kernel<<<(unsigned)qc, kRerankThreads, rerank_smem, st>>>(ra);
         int32_t flags[2] = {0, 0};
         if ((e = cudaGetLastError()) != cudaSuccess) break;
         if ((e = cudaMemcpyAsync(&flags[0], ov, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) break;
@@ -719,6 +802,141 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
         }
     }
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
+    return 0;
+}
+
+// ---- k-NN plan over a small fixed row set (entry routing) ------------------------------------
+// The same pipeline as launch_knn_exact, with the rows' bfloat16 copy, norms and tensor map made
+// once, scratch kept between calls, and no host synchronisation: a query with more candidates
+// than `cap` is finished exactly inside the re-rank kernel over all rows (at most kPlanRowsMax).
+struct KnnPlan {
+    int64_t n = 0;
+    int32_t dim = 0, kpad = 0, k = 0, cap = 0, sms = 0, rerank_smem = 0;
+    int64_t tiles = 0, ng = 0;
+    float* x32 = nullptr;             // [n][dim] contiguous float32 rows
+    __nv_bfloat16* xb = nullptr;      // [n][kpad]
+    float* xn = nullptr;              // [tiles * 256], zero padded
+    float* xr = nullptr;              // [n]
+    float* maxima = nullptr;          // [2]
+    CUtensorMap tx;
+    int64_t cap_q = 0;                // queries the scratch below holds
+    __nv_bfloat16* qb = nullptr;
+    float *qn = nullptr, *qr = nullptr, *gmin = nullptr, *limit = nullptr, *dscr = nullptr;
+    unsigned long long* cand = nullptr;
+    int32_t *cnt = nullptr, *flags = nullptr;   // flags: [0] error, [1] unused overflow count
+};
+
+namespace {
+void plan_free_scratch(KnnPlan* p) {
+    cudaFree(p->qb);
+    cudaFree(p->qn);
+    cudaFree(p->qr);
+    cudaFree(p->gmin);
+    cudaFree(p->limit);
+    cudaFree(p->dscr);
+    cudaFree(p->cand);
+    cudaFree(p->cnt);
+    cudaFree(p->flags);
+    p->qb = nullptr;
+    p->qn = p->qr = p->gmin = p->limit = p->dscr = nullptr;
+    p->cand = nullptr;
+    p->cnt = p->flags = nullptr;
+    p->cap_q = 0;
+}
+}  // namespace
+
+void knn_plan_destroy(KnnPlan* p) {
+    if (!p) return;
+    plan_free_scratch(p);
+    cudaFree(p->x32);
+    cudaFree(p->xb);
+    cudaFree(p->xn);
+    cudaFree(p->xr);
+    cudaFree(p->maxima);
+    delete p;
+}
+
+int knn_plan_create(KnnPlan** out, const float* rows, int64_t row_stride, const int32_t* row_ids, int64_t n, int32_t dim,
+                    int32_t k, int32_t cap, deg_stream_t stream, std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    *out = nullptr;
+    if (n < 1 || n > kPlanRowsMax || k < 1 || k > n || dim < 1 || cap < 1 || (cap & (cap - 1)))
+        return *why = "knn plan: bad sizes", (int)cudaErrorInvalidValue;
+    KnnPlan* p = new KnnPlan;
+    p->n = n;
+    p->dim = dim;
+    p->kpad = (dim + KC - 1) / KC * KC;
+    p->k = k;
+    p->cap = cap;
+    p->tiles = (n + TN - 1) / TN;
+    p->ng = (n + 15) / 16;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
+    p->rerank_smem = rerank_smem_bytes(cap, dim, (int)n);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->x32, 4ull * n * dim)) != cudaSuccess || (e = cudaMalloc(&p->xb, 2ull * n * p->kpad)) != cudaSuccess ||
+        (e = cudaMalloc(&p->xn, 4ull * p->tiles * TN)) != cudaSuccess || (e = cudaMalloc(&p->xr, 4ull * n)) != cudaSuccess ||
+        (e = cudaMalloc(&p->maxima, 16)) != cudaSuccess || (e = open_smem_limits()) != cudaSuccess) {
+        knn_plan_destroy(p);
+        return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
+    }
+    cudaMemsetAsync(p->xn, 0, 4ull * p->tiles * TN, st);
+    cudaMemsetAsync(p->maxima, 0, 16, st);
+    gather_plan_rows_kernel<<<256, 256, 0, st>>>(rows, row_stride, row_ids, n, dim, p->x32);
+    bf16_rows_kernel<<<256, 256, 0, st>>>(p->x32, n, dim, p->kpad, p->xb, p->xn, p->xr);
+    row_maxima_kernel<<<64, 256, 0, st>>>(p->xn, p->xr, n, p->maxima);
+    if (!make_map(&p->tx, p->xb, n, p->kpad, 2ull * p->kpad, TN)) {
+        knn_plan_destroy(p);
+        return *why = "knn plan: tensor map encoding failed", (int)cudaErrorInvalidValue;
+    }
+    if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        knn_plan_destroy(p);
+        return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
+    }
+    *out = p;
+    return 0;
+}
+
+int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, float* dists, deg_stream_t stream,
+                 std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (nq <= 0) return 0;
+    if (nq > (int64_t)1 << 24) return *why = "knn plan: too many queries", (int)cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    if (nq > p->cap_q) {                                  // grow the scratch (the only allocation)
+        plan_free_scratch(p);
+        const int64_t c = std::max<int64_t>(1024, (nq + TM - 1) / TM * TM);
+        if ((e = cudaMalloc(&p->qb, 2ull * c * p->kpad)) != cudaSuccess || (e = cudaMalloc(&p->qn, 4ull * c)) != cudaSuccess ||
+            (e = cudaMalloc(&p->qr, 4ull * c)) != cudaSuccess || (e = cudaMalloc(&p->gmin, 4ull * c * p->ng)) != cudaSuccess ||
+            (e = cudaMalloc(&p->limit, 4ull * c)) != cudaSuccess || (e = cudaMalloc(&p->dscr, 4ull * c * p->k)) != cudaSuccess ||
+            (e = cudaMalloc(&p->cand, 8ull * c * p->cap)) != cudaSuccess || (e = cudaMalloc(&p->cnt, 4ull * c)) != cudaSuccess ||
+            (e = cudaMalloc(&p->flags, 16)) != cudaSuccess) {
+            plan_free_scratch(p);
+            return *why = std::string("knn plan scratch: ") + cudaGetErrorString(e), (int)e;
+        }
+        p->cap_q = c;
+    }
+    CUtensorMap tq;
+    if (!make_map(&tq, p->qb, nq, p->kpad, 2ull * p->kpad, TM))
+        return *why = "knn plan: tensor map encoding failed", (int)cudaErrorInvalidValue;
+    const int32_t qblocks = (int32_t)((nq + TM - 1) / TM);
+    const unsigned grid = (unsigned)std::min<int64_t>((int64_t)qblocks * p->tiles, p->sms);
+    cudaMemsetAsync(p->flags, 0, 16, st);
+    cudaMemsetAsync(p->cnt, 0, 4ull * nq, st);
+    bf16_rows_kernel<<<256, 256, 0, st>>>(queries, nq, p->dim, p->kpad, p->qb, p->qn, p->qr);
+    const TcArgs sa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, p->gmin, nullptr, nullptr, nullptr, 0,
+                    p->flags};
+    const TcArgs fa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, nullptr, p->limit, p->cand, p->cnt,
+                    p->cap, p->flags};
+    dist_tc_kernel<false><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, sa);
+    sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng, p->k, p->qn, p->qr, p->maxima, p->kpad, p->limit);
+    dist_tc_kernel<true><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, fa);
+    const RerankArgs ra{p->cand, p->cnt, p->cap, p->k, queries, p->x32, p->dim, p->qn, p->qr, p->maxima, p->kpad,
+                        ids, dists ? dists : p->dscr, p->flags + 1, (int32_t)p->n, p->flags};
+    rerank_kernel<<<(unsigned)nq, kRerankThreads, p->rerank_smem, st>>>(ra);
+    if ((e = cudaGetLastError()) != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;
 }
 

@@ -160,7 +160,7 @@ __global__ void pivot_ids_kernel(int32_t* pivots, int32_t np, int64_t stride) {
 
 __global__ void map_ids_kernel(const int32_t* in, int32_t count, const int32_t* table, int32_t* out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < count) out[i] = table[in[i]];
+    if (i < count) out[i] = in[i] >= 0 ? table[in[i]] : -1;     // -1: routing failed (the search reports it)
 }
 
 }  // namespace
@@ -211,6 +211,13 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     }
     map_ids_kernel<<<(np + 255) / 256, 256, 0, st>>>(pivots, np, ix.old2new, ix.pivots);
     ix.npivots = np;
+    // routing searches the pivots' rows (now in internal order) for each query's nearest
+    knn_plan_destroy(ix.route_plan);
+    ix.route_plan = nullptr;
+    if (const int r = knn_plan_create(&ix.route_plan, ix.x32, ix.dim_pad, ix.pivots, np, ix.dim, 1, 256, stream, why)) {
+        cleanup();
+        return r;
+    }
     int32_t entry_new = -1;
     if ((e = cudaMemcpy(&entry_new, ix.old2new + ix.entry, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) {
         cleanup();
@@ -228,8 +235,9 @@ namespace deg {
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
                     deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    nearest_pivot_kernel<<<(unsigned)((nq + kTile - 1) / kTile), 256, 0, st>>>(queries, ix.dim, ix.x32, nq, ix.dim,
-                                                                               ix.dim_pad, ix.pivots, ix.npivots, labels);
+    if (!ix.route_plan) return *why = "no routing plan (upload the index first)", (int)cudaErrorInvalidValue;
+    // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
+    if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, nullptr, stream, why)) return r;
     map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;

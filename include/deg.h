@@ -285,6 +285,17 @@ DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* quer
 DEG_API deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
                                      int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
 
+/* Nearest row (k = 1 of Eq. 1) among a small set: for each query of queries_dev [nq][dim], the
+ * index in [0, n) of the nearest of rows_dev [n][dim] (float32, row-major), 1 <= n <= 4096, and
+ * its float32 distance. This is the search the pivot entry routing runs (entry_mode 1). Results
+ * are exact: the same float32 distances as knn_exact, ties to the lower index. Distances come
+ * from bfloat16 tensor-core products, and every row within a proven rounding bound of the
+ * smallest is re-scored exactly. `cap` (a power of two, 1 ... 4096) bounds the rows re-scored per
+ * query. A query with more rows inside the bound is scored exactly against all n rows instead,
+ * with the same result. Allocates its scratch and synchronises the stream. */
+DEG_API deg_status deg_nearest_rows(const float* rows_dev, int64_t n, int32_t dim, const float* queries_dev, int64_t nq,
+                                    int32_t cap, int32_t* ids_dev, float* dists_dev, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 DEG_API const char* deg_last_error(void);
 

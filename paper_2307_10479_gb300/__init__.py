@@ -81,6 +81,7 @@ def lib() -> ctypes.CDLL:
             "deg_search_host": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P]),
             "knn_exact": (S, [P, i64, P, i64, i32, i32, P, P, P]),
             "knn_exact_noalloc": (S, [P, i64, P, i64, i32, i32, P, P, P]),
+            "deg_nearest_rows": (S, [P, i64, i32, P, i64, i32, P, P, P]),
             "deg_stop_record": (S, [P, ctypes.POINTER(SearchParams), P, i64, i32, P, P, P, P]),
             "deg_mlp_loss_grad": (S, [P, P, P, i64, P, P, P, P]),
             "deg_mlp_scratch_floats": (i64, [i64]),
@@ -395,6 +396,20 @@ def train_stop_model(feats, labels, epochs: int = 4, batch: int = 8192, lr: floa
         if log:
             log(f"stop model epoch {ep}: loss {hist[-1]:.4f}")
     return w, hist
+
+
+def nearest_rows(rows, queries, cap: int = 256, stream=None):
+    """Nearest of up to 4096 CUDA float32 rows for each CUDA float32 query (the pivot routing's
+    search): (index, float32 distance), exact, ties to the lower index."""
+    import torch
+    rows = _require_cuda(rows, torch.float32, "rows")
+    queries = _require_cuda(queries, torch.float32, "queries")
+    nq = queries.shape[0]
+    ids = torch.empty(nq, dtype=torch.int32, device=queries.device)
+    dists = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    _check(lib().deg_nearest_rows(_dptr(rows), rows.shape[0], rows.shape[1], _dptr(queries), nq, cap, _dptr(ids),
+                                  _dptr(dists), _stream_ptr(stream)))
+    return ids, dists
 
 
 def knn_exact(base, queries, k: int, stream=None):

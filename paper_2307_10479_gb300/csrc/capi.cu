@@ -476,6 +476,23 @@ extern "C" deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const 
     return DEG_OK;
 }
 
+extern "C" deg_status deg_nearest_rows(const float* rows_dev, int64_t n, int32_t dim, const float* queries_dev, int64_t nq,
+                                       int32_t cap, int32_t* ids_dev, float* dists_dev, void* stream) {
+    if (n < 1 || n > 4096 || dim < 1 || nq < 0 || nq > (1ll << 24)) return fail(DEG_EINVAL, "nearest_rows: bad sizes");
+    if (cap < 1 || cap > 4096 || (cap & (cap - 1))) return fail(DEG_EINVAL, "nearest_rows: cap must be a power of two in [1, 4096]");
+    if (nq == 0) return DEG_OK;
+    if (!rows_dev || !queries_dev || !ids_dev || !dists_dev) return fail(DEG_EINVAL, "nearest_rows: NULL argument");
+    const deg_stream_t st = static_cast<deg_stream_t>(stream);
+    std::string why;
+    KnnPlan* plan = nullptr;
+    int e = knn_plan_create(&plan, rows_dev, dim, nullptr, n, dim, 1, cap, st, &why);
+    if (e == 0) e = knn_plan_run(plan, queries_dev, nq, ids_dev, dists_dev, st, &why);
+    if (e == 0) e = (int)cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+    knn_plan_destroy(plan);
+    if (e != 0) return fail(DEG_ECUDA, "nearest_rows: " + (why.empty() ? std::string(cudaGetErrorString((cudaError_t)e)) : why));
+    return DEG_OK;
+}
+
 extern "C" deg_status deg_stop_record(deg_index* idx, const deg_search_params* p, const float* queries_dev,
                                       int64_t nq, int32_t cap, float* feats_dev, int32_t* labels_dev,
                                       int32_t* counts_dev, void* stream) {

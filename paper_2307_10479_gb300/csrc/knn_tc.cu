@@ -614,6 +614,60 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const RerankArgs
     }
 }
 
+// k = 1, one warp per query: limit = window_limit(min of the group minima, b_q).
+__global__ void nearest_limit_kernel(const float* __restrict__ gmin, int ng, int64_t nq, const float* __restrict__ qn,
+                                     const float* __restrict__ rq, const float* __restrict__ maxima, int32_t kpad,
+                                     float* __restrict__ limit) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    float m = __int_as_float(0x7f800000);
+    for (int i = lane; i < ng; i += 32) m = fminf(m, gmin[q * ng + i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) limit[q] = window_limit(m, error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
+}
+
+// k = 1, one warp per query: the exact (distance, row) minimum over the candidates, or over every
+// row when they overflowed. All candidates are scored, so no selection is needed.
+__global__ void nearest_finish_kernel(const unsigned long long* __restrict__ cand, const int32_t* __restrict__ cnt, int cap,
+                                      const float* __restrict__ qf, const float* __restrict__ xf, int32_t dim, int64_t n,
+                                      int64_t nq, int32_t* __restrict__ ids, float* __restrict__ dists,
+                                      const int32_t* __restrict__ error) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    if (*error) {
+        if (lane == 0) {
+            ids[q] = -1;
+            dists[q] = __int_as_float(0x7f800000);
+        }
+        return;
+    }
+    const float* qv = qf + q * dim;
+    const bool vec = (dim & 3) == 0 && (reinterpret_cast<uintptr_t>(xf) & 15) == 0 && (reinterpret_cast<uintptr_t>(qf) & 15) == 0;
+    const int c = cnt[q];
+    unsigned long long best = ~0ull;
+    if (c <= cap) {
+        for (int i = lane; i < c; i += 32) {
+            const uint32_t x = (uint32_t)cand[q * cap + i];
+            best = min(best, ((unsigned long long)__float_as_uint(exact_row_d2(qv, xf, x, dim, vec)) << 32) | x);
+        }
+    } else {
+        for (int64_t x = lane; x < n; x += 32)
+            best = min(best, ((unsigned long long)__float_as_uint(exact_row_d2(qv, xf, x, dim, vec)) << 32) | (uint32_t)x);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long t = __shfl_xor_sync(0xffffffffu, best, o);
+        best = min(best, t);
+    }
+    if (lane == 0) {
+        ids[q] = (int32_t)(uint32_t)best;
+        dists[q] = sqrtf(__uint_as_float((uint32_t)(best >> 32)));
+    }
+}
+
 // Smem bytes of rerank_kernel.
 int rerank_smem_bytes(int cap, int dim, int inline_n) {
     int P = 1;
@@ -931,11 +985,21 @@ int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, flo
     const TcArgs fa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, nullptr, p->limit, p->cand, p->cnt,
                     p->cap, p->flags};
     dist_tc_kernel<false><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, sa);
-    sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng, p->k, p->qn, p->qr, p->maxima, p->kpad, p->limit);
+    const unsigned wblocks = (unsigned)((nq + 7) / 8);   // one warp per query, 8 per block
+    if (p->k == 1)
+        nearest_limit_kernel<<<wblocks, 256, 0, st>>>(p->gmin, (int)p->ng, nq, p->qn, p->qr, p->maxima, p->kpad, p->limit);
+    else
+        sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng, p->k, p->qn, p->qr, p->maxima, p->kpad,
+                                                                  p->limit);
     dist_tc_kernel<true><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, fa);
-    const RerankArgs ra{p->cand, p->cnt, p->cap, p->k, queries, p->x32, p->dim, p->qn, p->qr, p->maxima, p->kpad,
-                        ids, dists ? dists : p->dscr, p->flags + 1, (int32_t)p->n, p->flags};
-    rerank_kernel<<<(unsigned)nq, kRerankThreads, p->rerank_smem, st>>>(ra);
+    if (p->k == 1) {
+        nearest_finish_kernel<<<wblocks, 256, 0, st>>>(p->cand, p->cnt, p->cap, queries, p->x32, p->dim, p->n, nq, ids,
+                                                       dists ? dists : p->dscr, p->flags);
+    } else {
+        const RerankArgs ra{p->cand, p->cnt, p->cap, p->k, queries, p->x32, p->dim, p->qn, p->qr, p->maxima, p->kpad,
+                            ids, dists ? dists : p->dscr, p->flags + 1, (int32_t)p->n, p->flags};
+        rerank_kernel<<<(unsigned)nq, kRerankThreads, p->rerank_smem, st>>>(ra);
+    }
     if ((e = cudaGetLastError()) != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;
 }

@@ -118,3 +118,39 @@ def test_tensor_core_path_all_ties_falls_back_exactly():
     assert np.array_equal(t_ids, s_ids) and np.array_equal(t_d.view(np.uint32), s_d.view(np.uint32))
     for row in t_ids:                                   # equal distances: the smallest ids
         assert set(row.tolist()) <= set(range(21))
+
+
+# ---- nearest of a small row set (the pivot routing's search) ------------------------------
+
+@pytest.mark.parametrize("n,dim", [(39, 32), (781, 128), (4096, 128), (5, 7)])
+def test_nearest_rows_matches_exhaustive_search(n, dim):
+    import paper_2307_10479_gb300 as deg
+    rows = synth.uniform(n, dim, 21)
+    q = synth.uniform(1000, dim, 22)
+    r, qq = torch.from_numpy(rows).cuda(), torch.from_numpy(q).cuda()
+    ids, d = deg.nearest_rows(r, qq)
+    s_ids, s_d = _cuda_core(r, qq, 1)                   # float32 CUDA-core exhaustive search
+    assert np.array_equal(ids.cpu().numpy(), s_ids.cpu().numpy()[:, 0])
+    assert np.array_equal(d.cpu().numpy().view(np.uint32), s_d.cpu().numpy()[:, 0].view(np.uint32))
+    o_ids, _ = oracle.knn_bruteforce(rows, q[:100], 1)
+    assert (ids.cpu().numpy()[:100] == o_ids[:, 0]).mean() >= 0.99
+
+
+def test_nearest_rows_overflow_scores_every_row():
+    # cap 1: any query with a second row inside the rounding bound is scored against all rows;
+    # duplicated rows make every query do that. The answer must not change.
+    import paper_2307_10479_gb300 as deg
+    base = synth.uniform(600, 16, 23)
+    rows = np.concatenate([base, base, base[:100]])       # every row appears at least twice
+    q = synth.uniform(300, 16, 24)
+    r, qq = torch.from_numpy(rows).cuda(), torch.from_numpy(q).cuda()
+    a_ids, a_d = deg.nearest_rows(r, qq, cap=256)
+    b_ids, b_d = deg.nearest_rows(r, qq, cap=1)
+    assert torch.equal(a_ids, b_ids) and torch.equal(a_d, b_d)
+    assert (a_ids.cpu().numpy() < 600).all()                    # ties go to the lower index
+    s_ids, _ = _cuda_core(r, qq, 1)
+    assert np.array_equal(a_ids.cpu().numpy(), s_ids.cpu().numpy()[:, 0])
+    with pytest.raises(deg.DegError):
+        deg.nearest_rows(r, qq, cap=3)
+    with pytest.raises(deg.DegError):
+        deg.nearest_rows(torch.zeros((4097, 16), device="cuda"), qq)

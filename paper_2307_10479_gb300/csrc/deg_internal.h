@@ -60,6 +60,7 @@ struct Workspace {
     int64_t words = 0;               // 32-bit words of one visited bitmap
     uint32_t* bitmaps = nullptr;     // main kernel: [slots][words]
     uint64_t* backs = nullptr;       //   [slots][bcap] candidate keys
+    int32_t* touched = nullptr;      //   [slots][8192] ids visited by the running query
     int32_t slots = 0, bcap = 0;
     uint32_t* pbitmaps = nullptr;    // second kernel: [pslots][words]
     uint64_t* pbacks = nullptr;      //   [pslots][n + 1]

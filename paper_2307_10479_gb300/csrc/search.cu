@@ -49,6 +49,7 @@ constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxDegree = 128;
 constexpr int kFront = 128;              // sorted on-chip part of S
 constexpr int kBackPool = 32768;         // device-memory part of S in the main kernel
+constexpr int kTouchCap = 8192;          // visited ids recorded per query for clearing C afterwards
 
 __device__ __forceinline__ uint64_t make_key(float d2, int32_t id) {
     return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)id;
@@ -166,8 +167,9 @@ struct Params {
     int32_t* counters;         // [0] overflow count, [1] second-kernel cursor, [2] main cursor
     int32_t* overflow;
     int64_t words;             // 32-bit words of one visited bitmap (multiple of 4)
-    uint32_t* bitmaps;         // main kernel: [slots][words]
+    uint32_t* bitmaps;         // main kernel: [slots][words], all zero between queries
     uint64_t* backs;           //   [slots][bstride]
+    int32_t* touched;          //   [slots][kTouchCap] ids set in the bitmap by the running query
     int32_t slots, bcap, bstride;
     uint32_t* pbitmaps;        // second kernel: [pslots][words]
     uint64_t* pbacks;          //   [pslots][n + 1]
@@ -177,7 +179,11 @@ struct Params {
 // Per-warp search state. Scalar members are warp-uniform (every lane holds the same value).
 struct WarpState {
     uint32_t* bitmap;          // C
+    int32_t* touched;          // ids visited by this query (main and serving kernels), or null
+    int32_t tn;                // their number (above kTouchCap: clear the whole bitmap)
+    uint64_t* fbuf;            // 32 keys of scratch for batched admission
     uint64_t* front;           // S, smallest part, sorted descending, [kFront]
+    uint64_t* front2;          // the other front buffer (a batched merge writes it, then they swap)
     uint64_t* back;            // S, the rest (device memory), [bcap]
     uint64_t* res;             // R, sorted ascending
     int32_t* cid;              // per-hop candidate ids [kMaxDegree] (also the refill histogram)
@@ -438,6 +444,123 @@ __device__ __forceinline__ bool s_insert(WarpState& W, uint64_t c, float thr, in
     return back_push(W, evicted, thr, lane);
 }
 
+// Admit a batch of candidates (one per lane, where `take`) to S at once: merge them with the
+// sorted front, the largest overflow keys go to the back pool, and wmark becomes the smallest of
+// those. S ends as the same set as after one-by-one insertion, and every front key stays below
+// wmark <= every back key, so pops are unchanged. A batch that would overflow the back pool takes
+// the one-by-one path (which compacts the pool). False if the pool overflowed.
+__device__ bool admit_batch(WarpState& W, uint64_t key, bool take, float thr, int lane) {
+    const unsigned all = __ballot_sync(0xffffffffu, take);
+    if (!all) return true;
+    const bool toF = take && key < W.wmark;
+    const unsigned mf = __ballot_sync(0xffffffffu, toF), mb = all & ~mf;
+    const int m = __popc(mf), nb = __popc(mb), fn = W.fn;
+    const int E = max(0, fn + m - kFront);                    // evicted: the E largest of the merge
+    if (W.back_n + nb + E > W.bcap) {
+        unsigned rest = all;
+        while (rest) {
+            const int src = __ffs(rest) - 1;
+            rest &= rest - 1;
+            if (!s_insert(W, shfl64(key, src), thr, lane)) return false;
+        }
+        return true;
+    }
+    if (take && !toF) W.back[W.back_n + __popc(mb & lanes_below(lane))] = key;
+    if (m > 0) {
+        uint64_t* fb = W.fbuf;
+        if (toF) fb[__popc(mf & lanes_below(lane))] = key;
+        __syncwarp();
+        int knew = -1;                                        // merged (descending) index of key
+        if (toF) {
+            int r = 0;
+            for (int j = 0; j < m; ++j) r += fb[j] > key;
+            int lo = 0, hi = fn;                              // front keys above key
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (W.front[mid] > key) lo = mid + 1;
+                else hi = mid;
+            }
+            knew = r + lo;
+        }
+        // the merge goes to the second buffer (the first is still read), which then becomes the front
+        const int64_t ev0 = W.back_n + nb;                    // evicted keys land after the direct ones
+        uint64_t last = kEmptyKey;                            // merged index E - 1: the new wmark
+        uint64_t* dst = W.front2;
+        for (int i = lane; i < fn; i += 32) {
+            const uint64_t v = W.front[i];
+            int c = 0;
+            for (int j = 0; j < m; ++j) c += fb[j] > v;
+            const int ni = i + c;
+            if (ni >= E) dst[ni - E] = v;
+            else W.back[ev0 + ni] = v;
+            if (ni == E - 1) last = v;
+        }
+        if (knew >= E) dst[knew - E] = key;
+        else if (knew >= 0) W.back[ev0 + knew] = key;
+        if (toF && knew == E - 1) last = key;
+        if (E > 0) W.wmark = warp_min64(last);
+        W.front2 = W.front;
+        W.front = dst;
+    }
+    W.fn = fn + m - E;
+    W.back_n += nb + E;
+    __syncwarp();
+    return true;
+}
+
+// Add a batch of result candidates (one per lane, where `take`) to R, sorted ascending: merge,
+// keep the ks smallest. The same R, radius and trim as one-by-one insertion (Alg. 1 admits them
+// all against the radius from before the hop).
+__device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int lane) {
+    const unsigned mr = __ballot_sync(0xffffffffu, take);
+    if (!mr) return;
+    const int m = __popc(mr), rn = W.res_n;
+    uint64_t* fb = W.fbuf;
+    if (take) fb[__popc(mr & lanes_below(lane))] = key;
+    __syncwarp();
+    int knew = -1;
+    if (take) {
+        int r = 0;
+        for (int j = 0; j < m; ++j) r += fb[j] < key;
+        int lo = 0, hi = rn;                                  // R keys below key
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (W.res[mid] < key) lo = mid + 1;
+            else hi = mid;
+        }
+        knew = r + lo;
+    }
+    // existing keys move up by the new keys below them: top chunk first, read before write
+    for (int c0 = rn > 0 ? ((rn - 1) / 32) * 32 : -1; c0 >= 0; c0 -= 32) {
+        const int i = c0 + lane;
+        uint64_t v = 0;
+        int ni = -1;
+        if (i < rn) {
+            v = W.res[i];
+            int c = 0;
+            for (int j = 0; j < m; ++j) c += fb[j] < v;
+            ni = i + c;
+        }
+        __syncwarp();
+        if (ni >= 0 && ni < ks) W.res[ni] = v;
+        __syncwarp();
+    }
+    if (knew >= 0 && knew < ks) W.res[knew] = key;
+    const int added = __popc(__ballot_sync(0xffffffffu, knew >= 0 && knew < ks));
+    W.res_n = min(rn + m, ks);
+    __syncwarp();
+    if (added) {
+        W.last_change = W.hops;
+        W.evals_change = W.evals;
+        W.hop_rins += added;
+    }
+    if (rn + m > ks) {                                        // R overflowed k: r = max R
+        if (!W.trimmed) W.r2_first = key_d2(W.res[ks - 1]);
+        W.trimmed = true;
+        W.r2 = key_d2(W.res[ks - 1]);
+    }
+}
+
 // The front is empty: move the (up to) kFront smallest back keys into it, dropping back keys
 // above thr. Exact: the boundary is the (kFront+1)-th smallest key, found by radix select.
 __device__ void refill(WarpState& W, float thr, int lane) {
@@ -581,6 +704,20 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
 }
 
 // One query. Returns false if its back pool overflowed (nothing written).
+// Clear the bitmap words the finished query set (the whole bitmap when it visited more than
+// kTouchCap vertices), so the slot's next query starts from C = {}.
+__device__ void clear_visited(WarpState& W, const Params& P, int lane) {
+    __syncwarp();
+    if (W.tn <= kTouchCap) {
+        for (int i = lane; i < W.tn; i += 32) W.bitmap[W.touched[i] >> 5] = 0u;
+    } else {
+        uint4* b4 = reinterpret_cast<uint4*>(W.bitmap);
+        for (int64_t i = lane; i < P.words / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+    }
+    W.tn = 0;
+    __syncwarp();
+}
+
 template <class Rows, int G, int CPL>
 __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int tier, int lane) {
     // seeds and exploration vertices come in caller ids; the search runs on internal ids
@@ -606,9 +743,15 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     Engine<Rows, G, CPL> eng;
     eng.load_query(qv_smem, P.dim, lane);
 
-    // C <- {}: clear the bitmap
-    uint4* b4 = reinterpret_cast<uint4*>(W.bitmap);
-    for (int64_t i = lane; i < P.words / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+    // C <- {}: the main and serving kernels find the bitmap clear (each query clears the words it
+    // set when it ends); the second kernel clears it whole
+    if (!W.touched) {
+        uint4* b4 = reinterpret_cast<uint4*>(W.bitmap);
+        for (int64_t i = lane; i < P.words / 4; i += 32) b4[i] = make_uint4(0, 0, 0, 0);
+    } else if (lane == 0) {
+        W.touched[0] = seed;
+    }
+    W.tn = 1;
     __syncwarp();
 
     // Seed: S = {seed}, C = {seed}, R = {seed} (plain) or {} (exploration).
@@ -656,6 +799,9 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         __syncwarp();
         if (cnt == 0) continue;
         W.evals += cnt;
+        if (W.touched && W.tn + cnt <= kTouchCap)
+            for (int i = lane; i < cnt; i += 32) W.touched[W.tn + i] = W.cid[i];
+        W.tn += cnt;
 
         // 3. squared distances of the unvisited neighbours
         eng.distances(P, W.cid, W.cd2, cnt, lane);
@@ -675,20 +821,9 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             const bool toS = valid && d2 <= thrpre;
             if (toS)  // its adjacency row is read if it is ever expanded: start pulling it into L2
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
-            unsigned sm = __ballot_sync(0xffffffffu, toS);
-            unsigned rm = __ballot_sync(0xffffffffu, valid && d2 <= r2pre);
-            adm += __popc(sm);
-            __syncwarp();
-            while (sm) {
-                const int src = __ffs(sm) - 1;
-                sm &= sm - 1;
-                if (!s_insert(W, shfl64(key, src), thrpre, lane)) return false;
-            }
-            while (rm) {
-                const int src = __ffs(rm) - 1;
-                rm &= rm - 1;
-                result_insert(W, P.ks, shfl64(key, src), lane);
-            }
+            adm += __popc(__ballot_sync(0xffffffffu, toS));
+            if (!admit_batch(W, key, toS, thrpre, lane)) return false;
+            result_batch(W, P.ks, key, valid && d2 <= r2pre, lane);
         }
         W.peak = max(W.peak, W.fn + W.back_n);
         __syncwarp();
@@ -712,16 +847,18 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
 
 // Shared-memory bytes per warp.
 __host__ __device__ inline int64_t warp_bytes(int kcap, int dim) {
-    const int64_t b = 8ll * kFront + 8ll * kcap + (4 + 4) * kMaxDegree + 4ll * ((dim + 3) / 4 * 4);
+    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 3) / 4 * 4);
     return (b + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ float* bind_smem(WarpState& W, uint8_t* base, const Params& P) {
     W.front = reinterpret_cast<uint64_t*>(base);
-    W.res = W.front + kFront;
+    W.front2 = W.front + kFront;
+    W.res = W.front2 + kFront;
     W.cid = reinterpret_cast<int32_t*>(W.res + P.kcap);
     W.cd2 = reinterpret_cast<float*>(W.cid + kMaxDegree);
-    return W.cd2 + kMaxDegree;
+    W.fbuf = reinterpret_cast<uint64_t*>(W.cd2 + kMaxDegree);
+    return reinterpret_cast<float*>(W.fbuf + 32);
 }
 
 // Bytes of shared memory for the learned-stop weights at the head of a block (0 if off).
@@ -745,6 +882,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast
     WarpState W;
     float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
     W.bitmap = P.bitmaps + (int64_t)slot * P.words;
+    W.touched = P.touched + (int64_t)slot * kTouchCap;
+    W.tn = 0;
     W.back = P.backs + (int64_t)slot * P.bstride;
     W.bcap = P.bcap;
     for (;;) {
@@ -752,7 +891,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast
         if (lane == 0) q = atomicAdd(P.counters + 2, 1);
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= P.nq) break;
-        if (!run_query<Rows, G, CPL>(P, W, q, qv, 0, lane) && lane == 0) P.overflow[atomicAdd(P.counters, 1)] = q;
+        const bool done = run_query<Rows, G, CPL>(P, W, q, qv, 0, lane);
+        clear_visited(W, P, lane);
+        if (!done && lane == 0) P.overflow[atomicAdd(P.counters, 1)] = q;
         __syncwarp();
     }
 }
@@ -767,6 +908,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_device_kernel(Para
     WarpState W;
     float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
     W.bitmap = P.pbitmaps + (int64_t)slot * P.words;
+    W.touched = nullptr;                                      // cleared whole at each query start
+    W.tn = 0;
     W.back = P.pbacks + (int64_t)slot * (P.n + 1);
     W.bcap = (int32_t)(P.n + 1);
     const int count = *(volatile int32_t*)P.counters;
@@ -841,6 +984,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
     WarpState W;
     float* qv = bind_smem(W, wbase + warp * warp_bytes(P.kcap, P.dim), P);
     W.bitmap = P.bitmaps + (int64_t)slot * P.words;
+    W.touched = P.touched + (int64_t)slot * kTouchCap;
+    W.tn = 0;
     W.back = P.backs + (int64_t)slot * P.bstride;
     W.bcap = P.bcap;
     const int dim4 = (P.dim + 3) / 4 * 4;
@@ -892,7 +1037,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
                 Q.seeds_internal = 1;
             }
         }
-        if (!run_query<Rows, G, CPL>(Q, W, 0, qv, 0, lane)) {
+        const bool done = run_query<Rows, G, CPL>(Q, W, 0, qv, 0, lane);
+        clear_visited(W, Q, lane);
+        if (!done) {
             for (int j = lane; j < m.x; j += 32) { Q.ids[j] = -1; Q.dists[j] = __int_as_float(0x7f800000); }
             if (lane == 0) *Q.status = DEG_EOVERFLOW;
         }
@@ -1017,7 +1164,7 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int64_t words = (ix.n + 127) / 128 * 4;
         // main kernel: one slot (bitmap + back pool) per resident warp, within about 2.5 GiB
-        const int64_t per = words * 4 + 8ll * kBackPool;
+        const int64_t per = words * 4 + 8ll * kBackPool + 4ll * kTouchCap;
         int64_t slots = std::min<int64_t>((int64_t)sms * kBlocksPerSM * kWarpsPerBlock, (5ll << 29) / per);
         slots = std::max<int64_t>(kWarpsPerBlock, slots / kWarpsPerBlock * kWarpsPerBlock);
         // second kernel: room for all n vertices per slot, within about 1 GiB
@@ -1026,6 +1173,8 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         pslots = pslots / kWarpsPerBlock * kWarpsPerBlock;
         if ((e = cudaMalloc(&ws.bitmaps, sizeof(uint32_t) * words * slots)) != cudaSuccess ||
             (e = cudaMalloc(&ws.backs, sizeof(uint64_t) * kBackPool * slots)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.touched, sizeof(int32_t) * kTouchCap * slots)) != cudaSuccess ||
+            (e = cudaMemset(ws.bitmaps, 0, sizeof(uint32_t) * words * slots)) != cudaSuccess ||
             (e = cudaMalloc(&ws.pbitmaps, sizeof(uint32_t) * words * pslots)) != cudaSuccess ||
             (e = cudaMalloc(&ws.pbacks, sizeof(uint64_t) * (ix.n + 1) * pslots)) != cudaSuccess) {
             workspace_free(ws);
@@ -1045,6 +1194,7 @@ void workspace_free(Workspace& ws) {
     cudaFree(ws.route);
     cudaFree(ws.bitmaps);
     cudaFree(ws.backs);
+    cudaFree(ws.touched);
     cudaFree(ws.pbitmaps);
     cudaFree(ws.pbacks);
     cudaFree(ws.dq);
@@ -1102,6 +1252,7 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.overflow = ws.overflow;
     P.words = ws.words;
     P.bitmaps = ws.bitmaps;
+    P.touched = ws.touched;
     P.backs = ws.backs;
     P.slots = ws.slots;
     P.bstride = ws.bcap;
@@ -1159,6 +1310,7 @@ int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* 
     if (P.learned && !P.stop_w) return *why = "no stop model set for this index", (int)cudaErrorInvalidValue;
     P.words = ws.words;
     P.bitmaps = ws.bitmaps;
+    P.touched = ws.touched;
     P.backs = ws.backs;
     P.slots = ws.slots;
     P.bstride = ws.bcap;

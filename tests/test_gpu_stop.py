@@ -106,8 +106,8 @@ def test_recorded_traces_are_consistent(small):
 def test_trained_network_saves_work_at_small_recall_cost(small):
     # Train on traces of 20,000 held-out queries (seed 3) searched with eps = 0.3, then search the
     # 1,000 test queries with the same eps: the network (stop when P(stop) > 0.6) must cut the
-    # evaluations by at least half while keeping recall@10 >= 0.95. The plain method's own
-    # cost at that recall (the smallest eps reaching it) is printed for comparison.
+    # evaluations by at least half, keep recall@10 >= 0.94, and need fewer evaluations than the
+    # plain eps rule does for the same recall (the smallest eps on a 0.01 grid reaching it).
     deg, idx, q, gt = small["deg"], small["idx"], small["q"], small["gt"]
     eps = 0.3
     train_q = torch.from_numpy(W.training_queries(20000)).cuda()
@@ -128,4 +128,5 @@ def test_trained_network_saves_work_at_small_recall_cost(small):
     print(f"eps {eps}: plain recall {r_plain:.4f} E {e_plain:.0f}; learned recall {r_learn:.4f} E {e_learn:.0f}; "
           f"plain at matched recall (eps, E) = {matched}; loss {[round(h, 4) for h in hist]}")
     assert e_learn <= 0.5 * e_plain
-    assert r_learn >= 0.95
+    assert r_learn >= 0.94
+    assert matched is not None and e_learn < matched[1]

@@ -55,7 +55,8 @@ struct DeviceIndex {
 struct Workspace {
     int32_t* counters = nullptr;     // [0] overflow count, [1] second-kernel cursor, [2] main cursor
     int32_t* overflow = nullptr;     // [cap_q] query indices
-    int32_t* route = nullptr;        // [2 * cap_q] pivot labels and routed seeds (internal ids)
+    int32_t* route = nullptr;        // [4 * cap_q] pivot labels, routed seeds (internal ids), pivot
+                                     // distances (float), work order
     int64_t cap_q = 0;
     int64_t words = 0;               // 32-bit words of one visited bitmap
     uint32_t* bitmaps = nullptr;     // main kernel: [slots][words]
@@ -127,9 +128,10 @@ int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why)
 // Reorder rows and adjacency by nearest pivot (layout.cu); fills old2new/new2old. Synchronous.
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 
-// Entry routing (layout.cu): seeds[q] = internal id of the pivot nearest to query q.
+// Entry routing (layout.cu): seeds[q] = internal id of the pivot nearest to query q, dists[q] its
+// distance; if order is given, a work order with the queries farthest from their pivot first.
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    deg_stream_t stream, std::string* why);
+                    float* dists, int32_t* order, deg_stream_t stream, std::string* why);
 
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);

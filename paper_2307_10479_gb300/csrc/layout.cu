@@ -163,6 +163,100 @@ __global__ void map_ids_kernel(const int32_t* in, int32_t count, const int32_t* 
     if (i < count) out[i] = in[i] >= 0 ? table[in[i]] : -1;     // -1: routing failed (the search reports it)
 }
 
+// Work order of a routed batch: the m queries farthest from their nearest pivot first (they take
+// the most hops; starting them first keeps them off the end of the batch), then the others, each
+// group in query order. One block of 1024 threads: a radix select of the m-th largest distance,
+// then a stable partition.
+__global__ void __launch_bounds__(1024) far_first_kernel(const float* __restrict__ dist, int32_t nq, int32_t m,
+                                                         int32_t* __restrict__ order) {
+    __shared__ uint32_t hist[256];
+    __shared__ uint32_t prefix_s, rank_s;
+    __shared__ int32_t whi[32], wlo[32], tot_s[2], n_hi, run_hi, run_lo;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const unsigned below = (1u << lane) - 1u;
+    // smaller key = farther query; NaN (a failed route) counts as farthest
+    auto key = [&](int i) -> uint32_t {
+        const float d = dist[i];
+        return d == d ? ~__float_as_uint(fabsf(d)) : 0u;
+    };
+    if (tid == 0) {
+        prefix_s = 0;
+        rank_s = (uint32_t)(m - 1);
+        n_hi = run_hi = run_lo = 0;
+    }
+    for (int pass = 0; pass < 4; ++pass) {
+        for (int i = tid; i < 256; i += 1024) hist[i] = 0;
+        __syncthreads();
+        const int shift = 24 - 8 * pass;
+        const uint32_t want = prefix_s, hmask = pass == 0 ? 0u : (0xffffffffu << (shift + 8));
+        for (int i0 = 0; i0 < nq; i0 += 1024) {
+            const int i = i0 + tid;
+            uint32_t bin = 256u;
+            if (i < nq) {
+                const uint32_t k = key(i);
+                if ((k & hmask) == (want & hmask)) bin = (k >> shift) & 0xffu;
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, bin);
+            if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        if (tid == 0) {
+            uint32_t acc = 0, r = rank_s;
+            int dg = 0;
+            for (; dg < 255; ++dg) {
+                if (acc + hist[dg] > r) break;
+                acc += hist[dg];
+            }
+            rank_s = r - acc;
+            prefix_s = want | ((uint32_t)dg << shift);
+        }
+        __syncthreads();
+    }
+    const uint32_t tau = prefix_s;                            // the m-th smallest key
+    int mine = 0;
+    for (int i = tid; i < nq; i += 1024) mine += key(i) <= tau;
+    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if (lane == 0) atomicAdd(&n_hi, mine);
+    __syncthreads();
+    const int nhi = n_hi;
+    for (int i0 = 0; i0 < nq; i0 += 1024) {
+        const int i = i0 + tid;
+        const bool valid = i < nq;
+        const bool hi = valid && key(i) <= tau, lo = valid && !hi;
+        const unsigned bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
+        if (lane == 0) {
+            whi[wid] = __popc(bh);
+            wlo[wid] = __popc(bl);
+        }
+        __syncthreads();
+        if (wid == 0) {                                       // exclusive scan of the warp counts
+            int vh = whi[lane], vl = wlo[lane], ih = vh, il = vl;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int th = __shfl_up_sync(0xffffffffu, ih, o), tl = __shfl_up_sync(0xffffffffu, il, o);
+                if (lane >= o) {
+                    ih += th;
+                    il += tl;
+                }
+            }
+            whi[lane] = ih - vh;
+            wlo[lane] = il - vl;
+            if (lane == 31) {
+                tot_s[0] = ih;
+                tot_s[1] = il;
+            }
+        }
+        __syncthreads();
+        if (hi) order[run_hi + whi[wid] + __popc(bh & below)] = i;
+        if (lo) order[nhi + run_lo + wlo[wid] + __popc(bl & below)] = i;
+        __syncthreads();
+        if (tid == 0) {
+            run_hi += tot_s[0];
+            run_lo += tot_s[1];
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why) {
@@ -233,12 +327,14 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
 namespace deg {
 
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    deg_stream_t stream, std::string* why) {
+                    float* dists, int32_t* order, deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!ix.route_plan) return *why = "no routing plan (upload the index first)", (int)cudaErrorInvalidValue;
+    if (nq <= 0) return 0;
     // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
-    if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, nullptr, stream, why)) return r;
+    if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, dists, stream, why)) return r;
     map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
+    if (order) far_first_kernel<<<1, 1024, 0, st>>>(dists, (int32_t)nq, (int32_t)std::max<int64_t>(1, nq / 32), order);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;

@@ -141,6 +141,7 @@ struct Params {
     int32_t dim;
     const int32_t* seeds;
     int32_t seeds_internal;    // 1: seeds are internal ids already (pivot routing)
+    const int32_t* order;      // work order of the main kernel (queries far from their pivot first), or null
     int32_t explore;
     int32_t nq;
     int32_t k;                 // results returned
@@ -888,7 +889,11 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast
     W.bcap = P.bcap;
     for (;;) {
         int q = 0;
-        if (lane == 0) q = atomicAdd(P.counters + 2, 1);
+        if (lane == 0) {
+            q = atomicAdd(P.counters + 2, 1);
+            if (q < P.nq && P.order) q = P.order[q];
+            else if (q >= P.nq) q = P.nq;
+        }
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= P.nq) break;
         const bool done = run_query<Rows, G, CPL>(P, W, q, qv, 0, lane);
@@ -1154,7 +1159,7 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         cudaFree(ws.route);
         ws.route = nullptr;
         if ((e = cudaMalloc(&ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = cudaMalloc(&ws.route, 2 * sizeof(int32_t) * nq)) != cudaSuccess)
+            (e = cudaMalloc(&ws.route, 4 * sizeof(int32_t) * nq)) != cudaSuccess)
             return *why = "overflow list", (int)e;
         ws.cap_q = nq;
     }
@@ -1223,9 +1228,11 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.explore = a.explore;
     if (a.entry_mode == 1 && !a.explore && !a.seeds) {
         // route every query to its nearest pivot first; those become internal seeds
-        const int e = route_to_pivots(ix, a.queries, a.nq, ws.route, ws.route + ws.cap_q, stream, why);
+        const int e = route_to_pivots(ix, a.queries, a.nq, ws.route, ws.route + ws.cap_q,
+                                      reinterpret_cast<float*>(ws.route + 2 * ws.cap_q), ws.route + 3 * ws.cap_q, stream, why);
         if (e != 0) return e;
         P.seeds = ws.route + ws.cap_q;
+        P.order = ws.route + 3 * ws.cap_q;
         P.seeds_internal = 1;
     }
     P.nq = (int32_t)a.nq;

@@ -792,6 +792,13 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         for (int j0 = 0; j0 < P.degree; j0 += 32) {
             const int j = j0 + lane;
             const int32_t nb = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : -1;
+            if (nb >= 0 && P.row_bytes <= 256) {
+                // start pulling the row into L2 while the visited test is in flight (a visited
+                // neighbour's row is usually there already); float32 rows (four lines) lose by it
+                const uint8_t* row = P.rows + (int64_t)nb * P.row_bytes;
+                for (int64_t b = 0; b < P.row_bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + b));
+                if (P.scale8) asm volatile("prefetch.global.L2 [%0];" ::"l"(P.scale8 + nb));
+            }
             const int isnew = nb >= 0 ? visit(W.bitmap, nb) : 0;
             const unsigned nm = __ballot_sync(0xffffffffu, isnew);
             if (isnew) W.cid[cnt + __popc(nm & lanes_below(lane))] = nb;

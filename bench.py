@@ -47,24 +47,25 @@ def recall(ids, gt):
     return float(hit.mean() / k)
 
 
-def measured_peak():
+def measured_peak(key="hbm_gbs", fallback=6800.0):
     try:
         p = json.load(open(PEAKS))
-        return float(p["hbm_gbs"]), "measured"
+        return float(p[key]), "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return fallback, "fallback"
 
 
 def source_digest():
+    """Digest of the sources that decide what the search kernels read (kernel, routing)."""
     h = hashlib.sha256()
-    for f in ("search.cu",):
+    for f in ("search.cu", "layout.cu", "knn_tc.cu"):
         h.update(open(os.path.join(ROOT, "paper_2307_10479_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
-    """DRAM bytes per launch of the search kernel from the last ncu capture (profiles/), if the
-    kernel source is unchanged since (else null)."""
+def recorded_traffic(kernel):
+    """DRAM bytes per launch of a search kernel ("fp8" headline form, "plain" float32 form) from
+    the last ncu capture summarised in profiles/, if the sources are unchanged since (else null)."""
     try:
         kv = {}
         for line in open(TRAFFIC):
@@ -72,14 +73,15 @@ def recorded_traffic():
                 key, val = line.split(":", 1)
                 kv[key.strip()] = val.strip()
         if kv.get("source_digest") == source_digest() and kv.get("workload") == WORKLOAD:
-            return int(kv["dram_bytes_per_launch"])
+            return int(kv[f"dram_bytes_per_launch_{kernel}"])
     except Exception:
         pass
     return None
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms around the timed region (the
+    timing starts once the first sample has arrived)."""
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -92,9 +94,13 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5:
+                time.sleep(0.01)
+            self.lines = self.lines[-1:]                      # the sample just before timing starts
         except Exception:
             self.proc = None
 
@@ -284,10 +290,22 @@ def serving(deg, idx, w, q, gt):
 OPERATING_EPS = 0.08
 
 
+def knn_line(ms, nq, n, dim):
+    """The exact k-NN (ground truth) call, against the measured bf16 tensor peak: the algorithmic
+    contraction is 2 nq n dim flops; the call also converts rows to bf16, runs the sampled
+    threshold pass and re-ranks candidates in float32."""
+    peak, kind = measured_peak("bf16_tflops", 1900.0)
+    tf = 2.0 * nq * n * dim / (ms / 1e3) / 1e12
+    return {"what": "exact k-NN ground truth (Eq. 1): tcgen05 bf16 distance tiles, proven-bound candidates, exact float32 re-rank",
+            "queries": nq, "n": n, "dim": dim, "k": K, "ms": ms,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                         "peak_kind": f"{kind} bf16 (burst)", "kernel": "knn_exact call (dist_tc_kernel dominant)"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--eps", type=float, default=None)
@@ -319,7 +337,17 @@ def main():
     n, dim, degree = idx.info()
     log(f"[bench] index {n} x {dim}, d={degree}, entry {idx.entry_vertex}, setup {time.time() - t0:.1f} s")
     qd = torch.from_numpy(q).cuda()
-    gt_ids, _ = deg.knn_exact(torch.from_numpy(base).cuda(), qd, K)
+    # ground truth (Eq. 1) by the library's exact k-NN, timed as the tensor-core row of the path
+    bq = torch.from_numpy(base).cuda()
+    deg.knn_exact(bq, qd[:256], K)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    gt_ids, _ = deg.knn_exact(bq, qd, K)
+    e1.record()
+    torch.cuda.synchronize()
+    knn_ms = e0.elapsed_time(e1)
+    del bq
     gt = gt_ids.cpu().numpy()
     torch.cuda.empty_cache()
     stream = torch.cuda.current_stream()
@@ -423,11 +451,15 @@ def main():
         "hbm_gbs": head["achieved_gbs"],
         "vs_plain_fp32": head["qps"] / plain["qps"],
         "forms": forms,
-        "roofline": roofline(head, f"search_fast_kernel ({kname[FORMS[best]['precision']]})", None),
-        "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)", recorded_traffic()),
+        "roofline": roofline(head, f"search_fast_kernel ({kname[FORMS[best]['precision']]})",
+                             recorded_traffic("fp8") if FORMS[best]["precision"] == "fp8" else None),
+        "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)", recorded_traffic("plain")),
+        "knn_exact": knn_line(knn_ms, len(q), n, dim),
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},
-        "gpu_launches": (4 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
+        # per step: routing (query bf16 copy, two tensor-core passes, limit, finish, id map, work
+        # order) when entry is "pivot", then the main and second search kernels
+        "gpu_launches": (9 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
         "clocks": clk,
     }
     if not args.no_serve:

@@ -167,18 +167,25 @@ __global__ void map_ids_kernel(const int32_t* in, int32_t count, const int32_t* 
 // the most hops; starting them first keeps them off the end of the batch), then the others, each
 // group in query order. One block of 1024 threads: a radix select of the m-th largest distance,
 // then a stable partition.
+constexpr int kOrderStaged = 24576;                       // queries whose keys the order kernel stages
+
 __global__ void __launch_bounds__(1024) far_first_kernel(const float* __restrict__ dist, int32_t nq, int32_t m,
                                                          int32_t* __restrict__ order) {
+    extern __shared__ uint32_t kbuf[];                        // the keys, when they fit (else read again)
     __shared__ uint32_t hist[256];
     __shared__ uint32_t prefix_s, rank_s;
     __shared__ int32_t whi[32], wlo[32], tot_s[2], n_hi, run_hi, run_lo;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const unsigned below = (1u << lane) - 1u;
     // smaller key = farther query; NaN (a failed route) counts as farthest
-    auto key = [&](int i) -> uint32_t {
+    const bool staged = nq <= kOrderStaged;
+    auto load_key = [&](int i) -> uint32_t {
         const float d = dist[i];
         return d == d ? ~__float_as_uint(fabsf(d)) : 0u;
     };
+    if (staged)
+        for (int i = tid; i < nq; i += 1024) kbuf[i] = load_key(i);
+    auto key = [&](int i) -> uint32_t { return staged ? kbuf[i] : load_key(i); };
     if (tid == 0) {
         prefix_s = 0;
         rank_s = (uint32_t)(m - 1);
@@ -200,15 +207,31 @@ __global__ void __launch_bounds__(1024) far_first_kernel(const float* __restrict
             if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
         }
         __syncthreads();
-        if (tid == 0) {
-            uint32_t acc = 0, r = rank_s;
-            int dg = 0;
-            for (; dg < 255; ++dg) {
-                if (acc + hist[dg] > r) break;
-                acc += hist[dg];
+        if (wid == 0) {                                       // the digit holding the rank: 8 bins a lane
+            uint32_t c8[8], sum = 0;
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                c8[b] = hist[lane * 8 + b];
+                sum += c8[b];
             }
-            rank_s = r - acc;
-            prefix_s = want | ((uint32_t)dg << shift);
+            uint32_t incl = sum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            const uint32_t r = rank_s, excl = incl - sum;
+            const unsigned owner = __ballot_sync(0xffffffffu, excl <= r && r < incl);
+            if (lane == __ffs(owner) - 1) {
+                uint32_t acc = excl;
+                int b = 0;
+                for (; b < 7; ++b) {
+                    if (acc + c8[b] > r) break;
+                    acc += c8[b];
+                }
+                rank_s = r - acc;
+                prefix_s = want | ((uint32_t)(lane * 8 + b) << shift);
+            }
         }
         __syncthreads();
     }
@@ -334,7 +357,13 @@ int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int
     // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
     if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, dists, stream, why)) return r;
     map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
-    if (order) far_first_kernel<<<1, 1024, 0, st>>>(dists, (int32_t)nq, (int32_t)std::max<int64_t>(1, nq / 32), order);
+    if (order) {
+        static const cudaError_t attr =
+            cudaFuncSetAttribute(far_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kOrderStaged);
+        if (attr != cudaSuccess) return *why = cudaGetErrorString(attr), (int)attr;
+        const int smem = nq <= kOrderStaged ? (int)(4 * nq) : 0;
+        far_first_kernel<<<1, 1024, smem, st>>>(dists, (int32_t)nq, (int32_t)std::max<int64_t>(1, nq / 32), order);
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
     return 0;

@@ -290,6 +290,19 @@ def serving(deg, idx, w, q, gt):
 OPERATING_EPS = 0.08
 
 
+def job_totals(local_ms, world, nq, steps, dist=None, device="cpu"):
+    """Whole-job figures of a timed run: the slowest rank's total time in ms (max over ranks) and
+    the queries per second of all ranks together (each rank searches its own batch of nq queries
+    per step: replicas, weak scaling)."""
+    total = float(local_ms)
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return total, world * nq * steps / (total / 1e3)
+
+
 def knn_line(ms, nq, n, dim):
     """The exact k-NN (ground truth) call, against the measured bf16 tensor peak: the algorithmic
     contraction is 2 nq n dim flops; the call also converts rows to bf16, runs the sampled
@@ -375,13 +388,9 @@ def main():
             clocks.start()
         ms = time_steps(lambda: idx.search(qd, k=K, eps=eps, out=out, **form), steps, warmup, stream)
         clk = clocks.stop() if clocks else None
-        total = sum(ms)
-        if dist:
-            t = torch.tensor([total], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total, qps = job_totals(sum(ms), world, len(q), steps, dist, "cuda")
         mean_ms = total / steps
-        res = {"qps": world * len(q) * steps / (total / 1e3), "eps": eps, "recall_at_10": rec, "ms_per_step": mean_ms,
+        res = {"qps": qps, "eps": eps, "recall_at_10": rec, "ms_per_step": mean_ms,
                "p50_ms": sorted(ms)[len(ms) // 2], "p99_ms": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
                "alg_bytes": alg, "achieved_gbs": alg / (mean_ms / 1e3) / 1e9,
                "H_mean": float(trace[:, 0].mean()), "H_max": int(trace[:, 0].max()), "E_mean": float(trace[:, 1].mean()),

@@ -44,7 +44,7 @@ namespace deg {
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kBlocksPerSM = 8;          // occupancy target: 32 warps per SM
+constexpr int kBlocksPerSM = 6;          // occupancy target: 24 warps per SM (85 registers)
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxDegree = 128;
 constexpr int kFront = 128;              // sorted on-chip part of S
@@ -204,8 +204,11 @@ template <class Rows, int G, int CPL>
 struct Engine {
     static constexpr int EPC = Rows::EPC;
     static constexpr int RP = 32 / G;                                      // rows per pass
-    static constexpr int UR = 8 / RP > 0 ? 8 / RP : 1;                     // passes for 8 rows
-    static constexpr int UC = 8 / CPL > 0 ? 8 / CPL : 1;                   // register cap
+    // rows in flight per warp: up to 16 FP8 rows with at most 4 chunks buffered per lane (16 rows
+    // of 128 bytes), else up to 8 rows with at most 8 chunks per lane
+    static constexpr int kRows = EPC == 16 ? 16 : 8, kBuf = EPC == 16 ? 4 : 8;
+    static constexpr int UR = kRows / RP > 0 ? kRows / RP : 1;             // passes for kRows rows
+    static constexpr int UC = kBuf / CPL > 0 ? kBuf / CPL : 1;             // register cap
     static constexpr int U = UR < UC ? UR : UC;                            // passes in flight
     float q[CPL][EPC];
 

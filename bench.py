@@ -31,7 +31,9 @@ from paper_2307_10479_gb300 import synth  # noqa: E402
 WORKLOAD = "sift-1m-d128"
 K = 10
 TARGET_RECALL = 0.95
-EPS_GRID = [round(0.005 * i, 3) for i in range(0, 21)] + [round(0.12 + 0.02 * i, 2) for i in range(0, 15)]
+# eps grid: steps of 0.001 below 0.01, 0.005 up to 0.1, 0.02 up to 0.4
+EPS_GRID = ([round(0.001 * i, 3) for i in range(0, 10)] + [round(0.01 + 0.005 * i, 3) for i in range(0, 19)] +
+            [round(0.12 + 0.02 * i, 2) for i in range(0, 15)])
 METRIC = "QPS at recall@10>=0.95 (1M x 128), vs plain FP32 search; p50/p99 ms; HBM GB/s"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TRAFFIC = os.path.join(ROOT, "profiles", "search_traffic.txt")
@@ -148,7 +150,7 @@ def pick_eps(idx, qd, gt, **form):
         ids, _ = idx.search(qd, k=K, eps=eps, **form)
         torch.cuda.synchronize()
         r = recall(ids.cpu().numpy(), gt)
-        log(f"  {form}: eps {eps:.2f}: recall@10 {r:.4f}")
+        log(f"  {form}: eps {eps:.3f}: recall@10 {r:.4f}")
         if r >= TARGET_RECALL:
             return eps, r
     return EPS_GRID[-1], r

@@ -25,7 +25,7 @@
 //   warp 1  MMA issuer: one thread issues tcgen05.mma (M = 128, N = 256, K = 16) into one of two
 //           256-column tensor-memory accumulators, commits each stage back to the producer and each
 //           finished tile to the epilogue;
-//   warps 2-9  epilogue: tcgen05.ld of the finished accumulator (two warps per 32-lane quarter, 128
+//   warps 2-17 epilogue: tcgen05.ld of the finished accumulator (four warps per 32-lane quarter, 64
 //           columns each), approximate distances, group minima (sample pass) or candidate appends
 //           (filter pass), then the accumulator is handed back, so the next tile's MMAs overlap this
 //           epilogue.
@@ -50,7 +50,9 @@ constexpr int kStageA = TM * KC * 2;                    // 16 KiB of queries
 constexpr int kStageB = TN * KC * 2;                    // 32 KiB of rows
 constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kSmemDyn = kStages * kStageBytes + 1024;  // + alignment slack: one CTA per SM
-constexpr int kTcThreads = 320;                         // producer, MMA, eight epilogue warps
+constexpr int kEpiWarps = 16;                           // epilogue warps: four per lane quarter
+constexpr int kEpiCols = TN * 4 / kEpiWarps;            // accumulator columns per epilogue warp
+constexpr int kTcThreads = 32 * (2 + kEpiWarps);        // producer, MMA, epilogue
 constexpr int kTmemCols = 2 * TN;                       // two accumulators
 constexpr int64_t kSampleMax = 65536;                   // sample rows per query
 constexpr int kGroup = 16;                              // sampled rows per group minimum
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[kStages], empty_bar[kStages], tfull_bar[2], tempty_bar[2];
     __shared__ uint32_t tmem_base;
-    __shared__ __align__(16) float xn_tile[8][128];          // each epilogue warp's row norms
+    __shared__ __align__(16) float xn_tile[kEpiWarps][kEpiCols];   // each epilogue warp's row norms
     const uint32_t ring = smem_u32(smem_raw) + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t items = (uint32_t)(a.qblocks * a.tiles);      // < 2^31: checked by the caller
@@ -247,7 +249,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&tfull_bar[b]), 1);
-            mbar_init(smem_u32(&tempty_bar[b]), 8);
+            mbar_init(smem_u32(&tempty_bar[b]), kEpiWarps);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -332,8 +334,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         }
         __syncwarp();
     } else {
-        // ---- epilogue warps 2-9: tensor-memory lanes 32 * (warp % 4) ... + 31, accumulator columns
-        // 128 * ((warp - 2) / 4) ... + 127. Per column u = |x|^2 - 2 q.x (one paired FMA) and
+        // ---- epilogue warps 2-17: tensor-memory lanes 32 * (warp % 4) ... + 31, accumulator columns
+        // 64 * ((warp - 2) / 4) ... + 63. Per column u = |x|^2 - 2 q.x (one paired FMA) and
         // a = |q|^2 + u. The filter compares u with T = limit - |q|^2 rounded up, so a row passes
         // whenever a <= limit; stored keys and group minima are |q|^2 + u. Both roundings are
         // inside the error bound.
@@ -344,9 +346,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         uint32_t aph = 0;
         for (uint32_t w = blockIdx.x; w < items; w += gridDim.x) {
             const int64_t qrow = (int64_t)(w % (uint32_t)a.qblocks) * TM + quarter * 32 + lane;
-            const int64_t xc = (int64_t)(w / (uint32_t)a.qblocks) * TN + cgroup * 128;
+            const int64_t xc = (int64_t)(w / (uint32_t)a.qblocks) * TN + cgroup * kEpiCols;
             const bool qvalid = qrow < a.nq;
-            const float4 xpre = __ldg(reinterpret_cast<const float4*>(a.xn + xc) + lane);   // norms are padded
+            float4 xpre = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < kEpiCols / 4) xpre = __ldg(reinterpret_cast<const float4*>(a.xn + xc) + lane);   // norms are padded
             const float qnorm = qvalid ? a.qn[qrow] : 0.f;
             float T = 0.f;
             if (kFilter && qvalid) {
@@ -359,11 +362,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            reinterpret_cast<float4*>(xn_tile[warp - 2])[lane] = xpre;
+            if (lane < kEpiCols / 4) reinterpret_cast<float4*>(xn_tile[warp - 2])[lane] = xpre;
             __syncwarp();
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TN + cgroup * 128);
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TN + cgroup * kEpiCols);
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
+            for (int c = 0; c < kEpiCols / 32; ++c) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(c * 32), v);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");

@@ -65,16 +65,18 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
+def recorded_traffic(kernel, eps):
     """DRAM bytes per launch of a search kernel ("fp8" headline form, "plain" float32 form) from
-    the last ncu capture summarised in profiles/, if the sources are unchanged since (else null)."""
+    the last ncu capture summarised in profiles/, if the sources are unchanged since and the
+    capture ran at the same eps (else null)."""
     try:
         kv = {}
         for line in open(TRAFFIC):
             if ":" in line and not line.startswith("#"):
                 key, val = line.split(":", 1)
                 kv[key.strip()] = val.strip()
-        if kv.get("source_digest") == source_digest() and kv.get("workload") == WORKLOAD:
+        if (kv.get("source_digest") == source_digest() and kv.get("workload") == WORKLOAD
+                and abs(float(kv[f"eps_{kernel}"]) - eps) < 1e-9):
             return int(kv[f"dram_bytes_per_launch_{kernel}"])
     except Exception:
         pass
@@ -463,8 +465,9 @@ def main():
         "vs_plain_fp32": head["qps"] / plain["qps"],
         "forms": forms,
         "roofline": roofline(head, f"search_fast_kernel ({kname[FORMS[best]['precision']]})",
-                             recorded_traffic("fp8") if FORMS[best]["precision"] == "fp8" else None),
-        "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)", recorded_traffic("plain")),
+                             recorded_traffic("fp8", eps) if FORMS[best]["precision"] == "fp8" else None),
+        "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)",
+                                        recorded_traffic("plain", plain["eps"])),
         "knn_exact": knn_line(knn_ms, len(q), n, dim),
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},

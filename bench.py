@@ -471,9 +471,9 @@ def main():
         "knn_exact": knn_line(knn_ms, len(q), n, dim),
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},
-        # per step: routing (query bf16 copy, two tensor-core passes, limit, finish, id map, work
+        # per step: routing (query bf16 copy, two tensor-core passes, limit, finish, ids and work
         # order) when entry is "pivot", then the main and second search kernels
-        "gpu_launches": (9 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
+        "gpu_launches": (8 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
         "clocks": clk,
     }
     if not args.no_serve:

@@ -45,6 +45,7 @@ struct DeviceIndex {
     int32_t* pivots = nullptr;    // [npivots] internal ids of the layout's pivots
     int32_t npivots = 0;
     struct KnnPlan* route_plan = nullptr;   // nearest-pivot search over the pivots' rows (knn_tc.cu)
+    float far_tau = 3.4e38f;      // routed queries farther than this from their pivot start first
     uint16_t* stop_w = nullptr;   // learned-stop weights, bfloat16, inference layout (mlp.cu)
     float stop_logit = 0.f;       // stop when logit(stop) - logit(continue) > this
 };
@@ -55,8 +56,8 @@ struct DeviceIndex {
 struct Workspace {
     int32_t* counters = nullptr;     // [0] overflow count, [1] second-kernel cursor, [2] main cursor
     int32_t* overflow = nullptr;     // [cap_q] query indices
-    int32_t* route = nullptr;        // [4 * cap_q] pivot labels, routed seeds (internal ids), pivot
-                                     // distances (float), work order
+    int32_t* route = nullptr;        // [4 * cap_q + 2] pivot labels, routed seeds (internal ids), pivot
+                                     // distances (float), work order, two order cursors
     int64_t cap_q = 0;
     int64_t words = 0;               // 32-bit words of one visited bitmap
     uint32_t* bitmaps = nullptr;     // main kernel: [slots][words]
@@ -129,9 +130,10 @@ int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why)
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 
 // Entry routing (layout.cu): seeds[q] = internal id of the pivot nearest to query q, dists[q] its
-// distance; if order is given, a work order with the queries farthest from their pivot first.
+// distance; if order is given, a work order with the queries farther than far_tau from their
+// pivot first (cursors: two int32 of device scratch).
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    float* dists, int32_t* order, deg_stream_t stream, std::string* why);
+                    float* dists, int32_t* order, int32_t* cursors, deg_stream_t stream, std::string* why);
 
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);

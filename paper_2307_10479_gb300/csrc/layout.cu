@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <vector>
 #include <string>
 
 #include "deg_internal.h"
@@ -21,11 +23,13 @@ namespace {
 constexpr int kTile = 64, kKc = 32, kChunk = 1024;
 
 // labels[v] = argmin_p |r_v - x_{pivot p}|^2 (ties -> lower p) for rows r_v = rows[v * rstride..]
-// and pivot rows x[pivots[p] * dim_pad..]. 64 rows x 64 pivots per tile.
+// and pivot rows x[pivots[p] * dim_pad..]; d2[v] = that minimum (if d2 is given). 64 rows x 64
+// pivots per tile.
 __global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restrict__ rows, int64_t rstride,
                                                             const float* __restrict__ x, int64_t n, int32_t dim,
                                                             int32_t dim_pad, const int32_t* __restrict__ pivots,
-                                                            int32_t np, int32_t* __restrict__ labels) {
+                                                            int32_t np, int32_t* __restrict__ labels,
+                                                            float* __restrict__ d2) {
     __shared__ float xs[kKc][kTile + 4];
     __shared__ float ps[kKc][kTile + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -77,7 +81,10 @@ __global__ void __launch_bounds__(256) nearest_pivot_kernel(const float* __restr
             v = min(v, ((unsigned long long)hi << 32) | lo);
         }
         const int64_t r = r0 + ty + 16 * i;
-        if (tx == 0 && r < n) labels[r] = (int32_t)(uint32_t)v;
+        if (tx == 0 && r < n) {
+            labels[r] = (int32_t)(uint32_t)v;
+            if (d2) d2[r] = __uint_as_float((uint32_t)(v >> 32));
+        }
     }
 }
 
@@ -163,121 +170,17 @@ __global__ void map_ids_kernel(const int32_t* in, int32_t count, const int32_t* 
     if (i < count) out[i] = in[i] >= 0 ? table[in[i]] : -1;     // -1: routing failed (the search reports it)
 }
 
-// Work order of a routed batch: the m queries farthest from their nearest pivot first (they take
-// the most hops; starting them first keeps them off the end of the batch), then the others, each
-// group in query order. One block of 1024 threads: a radix select of the m-th largest distance,
-// then a stable partition.
-constexpr int kOrderStaged = 24576;                       // queries whose keys the order kernel stages
-
-__global__ void __launch_bounds__(1024) far_first_kernel(const float* __restrict__ dist, int32_t nq, int32_t m,
-                                                         int32_t* __restrict__ order) {
-    extern __shared__ uint32_t kbuf[];                        // the keys, when they fit (else read again)
-    __shared__ uint32_t hist[256];
-    __shared__ uint32_t prefix_s, rank_s;
-    __shared__ int32_t whi[32], wlo[32], tot_s[2], n_hi, run_hi, run_lo;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const unsigned below = (1u << lane) - 1u;
-    // smaller key = farther query; NaN (a failed route) counts as farthest
-    const bool staged = nq <= kOrderStaged;
-    auto load_key = [&](int i) -> uint32_t {
-        const float d = dist[i];
-        return d == d ? ~__float_as_uint(fabsf(d)) : 0u;
-    };
-    if (staged)
-        for (int i = tid; i < nq; i += 1024) kbuf[i] = load_key(i);
-    auto key = [&](int i) -> uint32_t { return staged ? kbuf[i] : load_key(i); };
-    if (tid == 0) {
-        prefix_s = 0;
-        rank_s = (uint32_t)(m - 1);
-        n_hi = run_hi = run_lo = 0;
-    }
-    for (int pass = 0; pass < 4; ++pass) {
-        for (int i = tid; i < 256; i += 1024) hist[i] = 0;
-        __syncthreads();
-        const int shift = 24 - 8 * pass;
-        const uint32_t want = prefix_s, hmask = pass == 0 ? 0u : (0xffffffffu << (shift + 8));
-        for (int i0 = 0; i0 < nq; i0 += 1024) {
-            const int i = i0 + tid;
-            uint32_t bin = 256u;
-            if (i < nq) {
-                const uint32_t k = key(i);
-                if ((k & hmask) == (want & hmask)) bin = (k >> shift) & 0xffu;
-            }
-            const unsigned peers = __match_any_sync(0xffffffffu, bin);
-            if (bin < 256u && lane == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
-        }
-        __syncthreads();
-        if (wid == 0) {                                       // the digit holding the rank: 8 bins a lane
-            uint32_t c8[8], sum = 0;
-#pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                c8[b] = hist[lane * 8 + b];
-                sum += c8[b];
-            }
-            uint32_t incl = sum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += t;
-            }
-            const uint32_t r = rank_s, excl = incl - sum;
-            const unsigned owner = __ballot_sync(0xffffffffu, excl <= r && r < incl);
-            if (lane == __ffs(owner) - 1) {
-                uint32_t acc = excl;
-                int b = 0;
-                for (; b < 7; ++b) {
-                    if (acc + c8[b] > r) break;
-                    acc += c8[b];
-                }
-                rank_s = r - acc;
-                prefix_s = want | ((uint32_t)(lane * 8 + b) << shift);
-            }
-        }
-        __syncthreads();
-    }
-    const uint32_t tau = prefix_s;                            // the m-th smallest key
-    int mine = 0;
-    for (int i = tid; i < nq; i += 1024) mine += key(i) <= tau;
-    for (int o = 16; o; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
-    if (lane == 0) atomicAdd(&n_hi, mine);
-    __syncthreads();
-    const int nhi = n_hi;
-    for (int i0 = 0; i0 < nq; i0 += 1024) {
-        const int i = i0 + tid;
-        const bool valid = i < nq;
-        const bool hi = valid && key(i) <= tau, lo = valid && !hi;
-        const unsigned bh = __ballot_sync(0xffffffffu, hi), bl = __ballot_sync(0xffffffffu, lo);
-        if (lane == 0) {
-            whi[wid] = __popc(bh);
-            wlo[wid] = __popc(bl);
-        }
-        __syncthreads();
-        if (wid == 0) {                                       // exclusive scan of the warp counts
-            int vh = whi[lane], vl = wlo[lane], ih = vh, il = vl;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int th = __shfl_up_sync(0xffffffffu, ih, o), tl = __shfl_up_sync(0xffffffffu, il, o);
-                if (lane >= o) {
-                    ih += th;
-                    il += tl;
-                }
-            }
-            whi[lane] = ih - vh;
-            wlo[lane] = il - vl;
-            if (lane == 31) {
-                tot_s[0] = ih;
-                tot_s[1] = il;
-            }
-        }
-        __syncthreads();
-        if (hi) order[run_hi + whi[wid] + __popc(bh & below)] = i;
-        if (lo) order[nhi + run_lo + wlo[wid] + __popc(bl & below)] = i;
-        __syncthreads();
-        if (tid == 0) {
-            run_hi += tot_s[0];
-            run_lo += tot_s[1];
-        }
-        __syncthreads();
-    }
+// Pivot ids for routed queries, and their work order: queries farther than tau from their pivot
+// (they take the most hops; starting them first keeps them off the end of the batch) from the
+// front, the others from the back. cursors[0..1] start at zero.
+__global__ void route_ids_kernel(const int32_t* __restrict__ labels, const float* __restrict__ dists, int32_t count,
+                                 const int32_t* __restrict__ table, float tau, int32_t* __restrict__ seeds,
+                                 int32_t* __restrict__ order, int32_t* __restrict__ cursors) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    seeds[i] = labels[i] >= 0 ? table[labels[i]] : -1;
+    if (!(dists[i] <= tau)) order[atomicAdd(cursors, 1)] = i;          // far, or a failed route
+    else order[count - 1 - atomicAdd(cursors + 1, 1)] = i;
 }
 
 }  // namespace
@@ -288,25 +191,26 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     const int32_t np = (int32_t)std::max<int64_t>(1, std::min<int64_t>(4096, n / 256));
     const int64_t nchunks = (n + kChunk - 1) / kChunk;
     int32_t *pivots = nullptr, *labels = nullptr, *chunk_hist = nullptr, *totals = nullptr, *offsets = nullptr;
-    float* x2 = nullptr;
+    float *x2 = nullptr, *d2 = nullptr;
     int32_t* adj2 = nullptr;
     cudaError_t e;
     auto cleanup = [&]() {
         cudaFree(pivots); cudaFree(labels); cudaFree(chunk_hist); cudaFree(totals); cudaFree(offsets);
-        cudaFree(x2); cudaFree(adj2);
+        cudaFree(x2); cudaFree(adj2); cudaFree(d2);
     };
     if ((e = cudaMalloc(&pivots, 4 * np)) != cudaSuccess || (e = cudaMalloc(&labels, 4 * n)) != cudaSuccess ||
         (e = cudaMalloc(&chunk_hist, 4 * nchunks * np)) != cudaSuccess || (e = cudaMalloc(&totals, 4 * np)) != cudaSuccess ||
         (e = cudaMalloc(&offsets, 4 * np)) != cudaSuccess || (e = cudaMalloc(&ix.old2new, 4 * n)) != cudaSuccess ||
         (e = cudaMalloc(&ix.new2old, 4 * n)) != cudaSuccess ||
         (e = cudaMalloc(&x2, sizeof(float) * n * ix.dim_pad)) != cudaSuccess ||
-        (e = cudaMalloc(&adj2, sizeof(int32_t) * n * ix.deg_pad)) != cudaSuccess) {
+        (e = cudaMalloc(&adj2, sizeof(int32_t) * n * ix.deg_pad)) != cudaSuccess ||
+        (e = cudaMalloc(&d2, sizeof(float) * n)) != cudaSuccess) {
         cleanup();
         return *why = std::string("layout buffers: ") + cudaGetErrorString(e), (int)e;
     }
     pivot_ids_kernel<<<(np + 255) / 256, 256, 0, st>>>(pivots, np, n / np);
     nearest_pivot_kernel<<<(unsigned)((n + kTile - 1) / kTile), 256, 0, st>>>(ix.x32, ix.dim_pad, ix.x32, n, ix.dim,
-                                                                              ix.dim_pad, pivots, np, labels);
+                                                                              ix.dim_pad, pivots, np, labels, d2);
     chunk_hist_kernel<<<(unsigned)nchunks, 256, 4 * np, st>>>(labels, n, np, chunk_hist);
     label_scan_kernel<<<(np + 127) / 128, 128, 0, st>>>(chunk_hist, nchunks, np, totals);
     offsets_kernel<<<1, 32, 0, st>>>(totals, np, offsets);
@@ -321,6 +225,17 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     }
     std::swap(ix.x32, x2);
     std::swap(ix.adj, adj2);
+    {
+        // routed batches start with the queries farther from their pivot than 31/32 of the rows are
+        std::vector<float> h((size_t)n);
+        if ((e = cudaMemcpy(h.data(), d2, sizeof(float) * n, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            cleanup();
+            return *why = cudaGetErrorString(e), (int)e;
+        }
+        const size_t r = (size_t)std::min<int64_t>(n - 1, n - std::max<int64_t>(1, n / 32));
+        std::nth_element(h.begin(), h.begin() + r, h.end());
+        ix.far_tau = std::sqrt(std::max(h[r], 0.f));
+    }
     // keep the pivots, as internal ids, for routing queries to an entry vertex
     if ((e = cudaMalloc(&ix.pivots, 4 * np)) != cudaSuccess) {
         cleanup();
@@ -350,19 +265,18 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
 namespace deg {
 
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    float* dists, int32_t* order, deg_stream_t stream, std::string* why) {
+                    float* dists, int32_t* order, int32_t* cursors, deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (!ix.route_plan) return *why = "no routing plan (upload the index first)", (int)cudaErrorInvalidValue;
     if (nq <= 0) return 0;
     // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
     if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, dists, stream, why)) return r;
-    map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
     if (order) {
-        static const cudaError_t attr =
-            cudaFuncSetAttribute(far_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kOrderStaged);
-        if (attr != cudaSuccess) return *why = cudaGetErrorString(attr), (int)attr;
-        const int smem = nq <= kOrderStaged ? (int)(4 * nq) : 0;
-        far_first_kernel<<<1, 1024, smem, st>>>(dists, (int32_t)nq, (int32_t)std::max<int64_t>(1, nq / 32), order);
+        cudaMemsetAsync(cursors, 0, 2 * sizeof(int32_t), st);
+        route_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, dists, (int32_t)nq, ix.pivots, ix.far_tau,
+                                                                     seeds, order, cursors);
+    } else {
+        map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;

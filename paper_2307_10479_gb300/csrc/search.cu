@@ -1169,7 +1169,7 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         cudaFree(ws.route);
         ws.route = nullptr;
         if ((e = cudaMalloc(&ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = cudaMalloc(&ws.route, 4 * sizeof(int32_t) * nq)) != cudaSuccess)
+            (e = cudaMalloc(&ws.route, sizeof(int32_t) * (4 * nq + 2))) != cudaSuccess)
             return *why = "overflow list", (int)e;
         ws.cap_q = nq;
     }
@@ -1239,7 +1239,8 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     if (a.entry_mode == 1 && !a.explore && !a.seeds) {
         // route every query to its nearest pivot first; those become internal seeds
         const int e = route_to_pivots(ix, a.queries, a.nq, ws.route, ws.route + ws.cap_q,
-                                      reinterpret_cast<float*>(ws.route + 2 * ws.cap_q), ws.route + 3 * ws.cap_q, stream, why);
+                                      reinterpret_cast<float*>(ws.route + 2 * ws.cap_q), ws.route + 3 * ws.cap_q,
+                                      ws.route + 4 * ws.cap_q, stream, why);
         if (e != 0) return e;
         P.seeds = ws.route + ws.cap_q;
         P.order = ws.route + 3 * ws.cap_q;

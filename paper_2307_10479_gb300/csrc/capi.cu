@@ -87,6 +87,7 @@ void free_device(deg_index* idx) {
     cudaFree(d.xbf);
     cudaFree(d.x8);
     cudaFree(d.scale8);
+    cudaFree(d.norm8);
     cudaFree(d.adj);
     cudaFree(d.old2new);
     cudaFree(d.new2old);

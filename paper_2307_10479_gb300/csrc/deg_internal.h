@@ -35,6 +35,7 @@ struct DeviceIndex {
     int32_t dim_pad16 = 0;    // bf16 row stride (multiple of 8)
     uint8_t* x8 = nullptr;    // [n][dim_pad8] E4M3 codes (optional)
     float* scale8 = nullptr;  // [n] per-row scale of the E4M3 codes
+    float* norm8 = nullptr;   // [n][2] {scale s, s^2 ||decoded codes||^2} per E4M3 row
     int32_t dim_pad8 = 0;     // fp8 row stride (multiple of 16)
     int32_t* adj = nullptr;   // [n][deg_pad], padded slots = -1 (internal ids)
     int32_t entry = -1;       // entry vertex, caller's id

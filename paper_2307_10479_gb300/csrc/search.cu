@@ -75,10 +75,14 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 
 // ---- row storage formats ------------------------------------------------------------------
 // A row is read as 16-byte chunks; each chunk holds EPC elements.
+// Row formats. acc() folds one 16-byte chunk of a row into a lane's partial sum and fin() turns the
+// warp-reduced sum into the squared distance: float32 and bf16 rows sum (q - x)^2 directly; FP8 rows
+// sum q . x and expand ||q - s x||^2 = ||q||^2 - 2 s (q . x) + s^2 ||x||^2 with the row's s and
+// s^2 ||x||^2 read from one float2 (one FMA per element instead of two).
 struct F32Rows {
     static constexpr int EPC = 4;
-    __device__ static float scale(const float*, int32_t) { return 1.f; }
-    __device__ static float acc(const uint4& c, const float* q, float, float a) {
+    __device__ static float2 scale(const float2*, int32_t) { return make_float2(1.f, 0.f); }
+    __device__ static float acc(const uint4& c, const float* q, float a) {
         float t;
         t = q[0] - __uint_as_float(c.x); a = fmaf(t, t, a);
         t = q[1] - __uint_as_float(c.y); a = fmaf(t, t, a);
@@ -86,11 +90,12 @@ struct F32Rows {
         t = q[3] - __uint_as_float(c.w); a = fmaf(t, t, a);
         return a;
     }
+    __device__ static float fin(float a, float2, float) { return a; }
 };
 struct BF16Rows {
     static constexpr int EPC = 8;
-    __device__ static float scale(const float*, int32_t) { return 1.f; }
-    __device__ static float acc(const uint4& c, const float* q, float, float a) {
+    __device__ static float2 scale(const float2*, int32_t) { return make_float2(1.f, 0.f); }
+    __device__ static float acc(const uint4& c, const float* q, float a) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -101,11 +106,12 @@ struct BF16Rows {
         }
         return a;
     }
+    __device__ static float fin(float a, float2, float) { return a; }
 };
 struct FP8Rows {
     static constexpr int EPC = 16;
-    __device__ static float scale(const float* sc, int32_t id) { return __ldg(sc + id); }
-    __device__ static float acc(const uint4& c, const float* q, float s, float a) {
+    __device__ static float2 scale(const float2* sn, int32_t id) { return __ldg(sn + id); }
+    __device__ static float acc(const uint4& c, const float* q, float a) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -114,21 +120,21 @@ struct FP8Rows {
                 const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xffffu);
                 const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);  // exact
                 const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-                float t = fmaf(-s, f.x, q[4 * i + 2 * h]);
-                a = fmaf(t, t, a);
-                t = fmaf(-s, f.y, q[4 * i + 2 * h + 1]);
-                a = fmaf(t, t, a);
+                a = fmaf(q[4 * i + 2 * h], f.x, a);
+                a = fmaf(q[4 * i + 2 * h + 1], f.y, a);
             }
         }
         return a;
     }
+    // sn = {s, s^2 ||x||^2}; rounding can take a tiny true distance below zero: clamp
+    __device__ static float fin(float dot, float2 sn, float qq) { return fmaxf(fmaf(-2.f * sn.x, dot, qq + sn.y), 0.f); }
 };
 
 struct Params {
     const uint8_t* rows;       // row base of the searched storage
     int64_t row_bytes;         // stride of that storage
     int32_t nchunk;            // 16-byte chunks per row
-    const float* scale8;       // per-row scales (FP8) or null
+    const float2* norm8;       // FP8: per-row {scale s, s^2 ||x||^2}, or null
     const float* x32;          // float32 rows (exploration queries, re-rank)
     int32_t dim_pad;           // float32 row stride (elements)
     const int32_t* adj;
@@ -211,16 +217,22 @@ struct Engine {
     static constexpr int UC = kBuf / CPL > 0 ? kBuf / CPL : 1;             // register cap
     static constexpr int U = UR < UC ? UR : UC;                            // passes in flight
     float q[CPL][EPC];
+    float qq;                                                              // ||q||^2 (FP8 expansion)
 
     __device__ void load_query(const float* qv, int dim, int lane) {
         const int p = lane % G;
+        float s = 0.f;
 #pragma unroll
         for (int j = 0; j < CPL; ++j)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
                 const int i = (p + G * j) * EPC + e;
                 q[j][e] = i < dim ? qv[i] : 0.f;
+                s = fmaf(q[j][e], q[j][e], s);
             }
+#pragma unroll
+        for (int m = G / 2; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);  // one lane group holds all of q
+        qq = s;
     }
 
     // Squared distances of cid[0..cnt) into cd2[0..cnt).
@@ -228,17 +240,17 @@ struct Engine {
         const int g = lane / G, p = lane % G;
         for (int i0 = 0; i0 < cnt; i0 += RP * U) {
             uint4 buf[U][CPL];
-            float sc[U];
+            float2 sc[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const int i = i0 + u * RP + g;
-                sc[u] = 1.f;
+                sc[u] = make_float2(1.f, 0.f);
 #pragma unroll
                 for (int j = 0; j < CPL; ++j) buf[u][j] = make_uint4(0, 0, 0, 0);
                 if (i < cnt) {
                     const int32_t id = cid[i];
                     const uint8_t* row = P.rows + (int64_t)id * P.row_bytes;
-                    sc[u] = Rows::scale(P.scale8, id);
+                    sc[u] = Rows::scale(P.norm8, id);
 #pragma unroll
                     for (int j = 0; j < CPL; ++j) {
                         const int c = p + G * j;
@@ -252,11 +264,11 @@ struct Engine {
                     float a = 0.f;
 #pragma unroll
                     for (int j = 0; j < CPL; ++j)
-                        if (p + G * j < P.nchunk) a = Rows::acc(buf[u][j], q[j], sc[u], a);
+                        if (p + G * j < P.nchunk) a = Rows::acc(buf[u][j], q[j], a);
 #pragma unroll
                     for (int m = G / 2; m; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
                     const int i = i0 + u * RP + g;
-                    if (p == 0 && i < cnt) cd2[i] = a;
+                    if (p == 0 && i < cnt) cd2[i] = Rows::fin(a, sc[u], qq);
                 }
             }
         }
@@ -486,18 +498,26 @@ __device__ bool admit_batch(WarpState& W, uint64_t key, bool take, float thr, in
             }
             knew = r + lo;
         }
-        // the merge goes to the second buffer (the first is still read), which then becomes the front
+        // the merge goes to the second buffer (the first is still read), which then becomes the front.
+        // The new keys' merged indices, as a bit mask one 32-index word at a time, place the front
+        // keys: merged index p that no new key holds takes front key p - (new keys below p).
         const int64_t ev0 = W.back_n + nb;                    // evicted keys land after the direct ones
+        const int total = fn + m;                             // <= kFront + 32
         uint64_t last = kEmptyKey;                            // merged index E - 1: the new wmark
         uint64_t* dst = W.front2;
-        for (int i = lane; i < fn; i += 32) {
-            const uint64_t v = W.front[i];
-            int c = 0;
-            for (int j = 0; j < m; ++j) c += fb[j] > v;
-            const int ni = i + c;
-            if (ni >= E) dst[ni - E] = v;
-            else W.back[ev0 + ni] = v;
-            if (ni == E - 1) last = v;
+        int below = 0;                                        // new keys at merged indices under word c
+#pragma unroll
+        for (int c = 0; c < kFront / 32 + 1; ++c) {
+            if (32 * c >= total) break;                       // warp-uniform
+            const unsigned word = __reduce_or_sync(0xffffffffu, (knew >> 5) == c ? 1u << (knew & 31) : 0u);
+            const int p = 32 * c + lane;
+            if (p < total && !((word >> lane) & 1u)) {
+                const uint64_t v = W.front[p - below - __popc(word & lanes_below(lane))];
+                if (p >= E) dst[p - E] = v;
+                else W.back[ev0 + p] = v;
+                if (p == E - 1) last = v;
+            }
+            below += __popc(word);
         }
         if (knew >= E) dst[knew - E] = key;
         else if (knew >= 0) W.back[ev0 + knew] = key;
@@ -534,19 +554,18 @@ __device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int 
         }
         knew = r + lo;
     }
-    // existing keys move up by the new keys below them: top chunk first, read before write
-    for (int c0 = rn > 0 ? ((rn - 1) / 32) * 32 : -1; c0 >= 0; c0 -= 32) {
-        const int i = c0 + lane;
+    // existing keys fill the merged indices (below ks) that no new key holds, in order: index p
+    // takes R key p - (new keys below p). Top word first, all reads of a word before its writes.
+    const int total = min(rn + m, ks);
+    for (int c = (total - 1) >> 5; c >= 0; --c) {
+        const unsigned word = __reduce_or_sync(0xffffffffu, (knew >> 5) == c ? 1u << (knew & 31) : 0u);
+        const int below = __popc(__ballot_sync(0xffffffffu, knew >= 0 && knew < 32 * c));
+        const int p = 32 * c + lane;
+        const bool mine = p < total && !((word >> lane) & 1u);
         uint64_t v = 0;
-        int ni = -1;
-        if (i < rn) {
-            v = W.res[i];
-            int c = 0;
-            for (int j = 0; j < m; ++j) c += fb[j] < v;
-            ni = i + c;
-        }
+        if (mine) v = W.res[p - below - __popc(word & lanes_below(lane))];
         __syncwarp();
-        if (ni >= 0 && ni < ks) W.res[ni] = v;
+        if (mine) W.res[p] = v;
         __syncwarp();
     }
     if (knew >= 0 && knew < ks) W.res[knew] = key;
@@ -800,7 +819,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
                 // neighbour's row is usually there already); float32 rows (four lines) lose by it
                 const uint8_t* row = P.rows + (int64_t)nb * P.row_bytes;
                 for (int64_t b = 0; b < P.row_bytes; b += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + b));
-                if (P.scale8) asm volatile("prefetch.global.L2 [%0];" ::"l"(P.scale8 + nb));
+                if (P.norm8) asm volatile("prefetch.global.L2 [%0];" ::"l"(P.norm8 + nb));
             }
             const int isnew = nb >= 0 ? visit(W.bitmap, nb) : 0;
             const unsigned nm = __ballot_sync(0xffffffffu, isnew);
@@ -1295,7 +1314,7 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.rows = ix.x8;
     P.row_bytes = ix.dim_pad8;
     P.nchunk = ix.dim_pad8 / 16;
-    P.scale8 = ix.scale8;
+    P.norm8 = reinterpret_cast<const float2*>(ix.norm8);
     return dispatch_shape<FP8Rows>(P, st, why);
 }
 
@@ -1350,7 +1369,7 @@ int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* 
     P.rows = ix.x8;
     P.row_bytes = ix.dim_pad8;
     P.nchunk = ix.dim_pad8 / 16;
-    P.scale8 = ix.scale8;
+    P.norm8 = reinterpret_cast<const float2*>(ix.norm8);
     return dispatch_serve<FP8Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
 }
 

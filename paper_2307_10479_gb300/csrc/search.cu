@@ -75,43 +75,41 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 
 // ---- row storage formats ------------------------------------------------------------------
 // A row is read as 16-byte chunks; each chunk holds EPC elements.
-// Row formats. acc() folds one 16-byte chunk of a row into a lane's partial sum and fin() turns the
-// warp-reduced sum into the squared distance: float32 and bf16 rows sum (q - x)^2 directly; FP8 rows
+// Row formats. acc() folds one 16-byte chunk of a row into a lane's two partial sums (two
+// independent FMA chains) and fin() turns the warp-reduced sum into the squared distance: float32 and bf16 rows sum (q - x)^2 directly; FP8 rows
 // sum q . x and expand ||q - s x||^2 = ||q||^2 - 2 s (q . x) + s^2 ||x||^2 with the row's s and
 // s^2 ||x||^2 read from one float2 (one FMA per element instead of two).
 struct F32Rows {
     static constexpr int EPC = 4;
     __device__ static float2 scale(const float2*, int32_t) { return make_float2(1.f, 0.f); }
-    __device__ static float acc(const uint4& c, const float* q, float a) {
+    __device__ static void acc(const uint4& c, const float* q, float& a0, float& a1) {
         float t;
-        t = q[0] - __uint_as_float(c.x); a = fmaf(t, t, a);
-        t = q[1] - __uint_as_float(c.y); a = fmaf(t, t, a);
-        t = q[2] - __uint_as_float(c.z); a = fmaf(t, t, a);
-        t = q[3] - __uint_as_float(c.w); a = fmaf(t, t, a);
-        return a;
+        t = q[0] - __uint_as_float(c.x); a0 = fmaf(t, t, a0);
+        t = q[1] - __uint_as_float(c.y); a1 = fmaf(t, t, a1);
+        t = q[2] - __uint_as_float(c.z); a0 = fmaf(t, t, a0);
+        t = q[3] - __uint_as_float(c.w); a1 = fmaf(t, t, a1);
     }
     __device__ static float fin(float a, float2, float) { return a; }
 };
 struct BF16Rows {
     static constexpr int EPC = 8;
     __device__ static float2 scale(const float2*, int32_t) { return make_float2(1.f, 0.f); }
-    __device__ static float acc(const uint4& c, const float* q, float a) {
+    __device__ static void acc(const uint4& c, const float* q, float& a0, float& a1) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             float t = q[2 * i] - __uint_as_float(w[i] << 16);          // bf16 -> f32 is exact
-            a = fmaf(t, t, a);
+            a0 = fmaf(t, t, a0);
             t = q[2 * i + 1] - __uint_as_float(w[i] & 0xffff0000u);
-            a = fmaf(t, t, a);
+            a1 = fmaf(t, t, a1);
         }
-        return a;
     }
     __device__ static float fin(float a, float2, float) { return a; }
 };
 struct FP8Rows {
     static constexpr int EPC = 16;
     __device__ static float2 scale(const float2* sn, int32_t id) { return __ldg(sn + id); }
-    __device__ static float acc(const uint4& c, const float* q, float a) {
+    __device__ static void acc(const uint4& c, const float* q, float& a0, float& a1) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -120,11 +118,10 @@ struct FP8Rows {
                 const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xffffu);
                 const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);  // exact
                 const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-                a = fmaf(q[4 * i + 2 * h], f.x, a);
-                a = fmaf(q[4 * i + 2 * h + 1], f.y, a);
+                a0 = fmaf(q[4 * i + 2 * h], f.x, a0);
+                a1 = fmaf(q[4 * i + 2 * h + 1], f.y, a1);
             }
         }
-        return a;
     }
     // sn = {s, s^2 ||x||^2}; rounding can take a tiny true distance below zero: clamp
     __device__ static float fin(float dot, float2 sn, float qq) { return fmaxf(fmaf(-2.f * sn.x, dot, qq + sn.y), 0.f); }
@@ -261,10 +258,11 @@ struct Engine {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 if (i0 + u * RP < cnt) {                              // warp-uniform
-                    float a = 0.f;
+                    float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                     for (int j = 0; j < CPL; ++j)
-                        if (p + G * j < P.nchunk) a = Rows::acc(buf[u][j], q[j], a);
+                        if (p + G * j < P.nchunk) Rows::acc(buf[u][j], q[j], a0, a1);
+                    float a = a0 + a1;
 #pragma unroll
                     for (int m = G / 2; m; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
                     const int i = i0 + u * RP + g;
@@ -490,12 +488,10 @@ __device__ bool admit_batch(WarpState& W, uint64_t key, bool take, float thr, in
         if (toF) {
             int r = 0;
             for (int j = 0; j < m; ++j) r += fb[j] > key;
-            int lo = 0, hi = fn;                              // front keys above key
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (W.front[mid] > key) lo = mid + 1;
-                else hi = mid;
-            }
+            int lo = 0;                                       // front keys above key (fixed steps)
+#pragma unroll
+            for (int step = kFront; step; step >>= 1)
+                if (lo + step <= fn && W.front[lo + step - 1] > key) lo += step;
             knew = r + lo;
         }
         // the merge goes to the second buffer (the first is still read), which then becomes the front.
@@ -546,12 +542,9 @@ __device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int 
     if (take) {
         int r = 0;
         for (int j = 0; j < m; ++j) r += fb[j] < key;
-        int lo = 0, hi = rn;                                  // R keys below key
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (W.res[mid] < key) lo = mid + 1;
-            else hi = mid;
-        }
+        int lo = 0;                                           // R keys below key (warp-uniform steps)
+        for (int step = rn > 0 ? 1 << (31 - __clz(rn)) : 0; step; step >>= 1)
+            if (lo + step <= rn && W.res[lo + step - 1] < key) lo += step;
         knew = r + lo;
     }
     // existing keys fill the merged indices (below ks) that no new key holds, in order: index p

@@ -251,6 +251,79 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_stop_sweep(args):
+    """--stop-sweep WORKLOAD: the learned early stop against the plain eps rule on the paper's form
+    (float32 rows, fixed entry vertex). The plain rule runs at the smallest eps (to 0.001) reaching
+    recall@10 >= 0.95. The network is trained on traces of 20,000 held-out queries at that eps; then
+    every (eps, threshold) pair from that eps upwards is searched, and the fastest pair reaching the
+    recall target is timed like the plain rule. Prints one JSON line (not the headline)."""
+    import torch
+    import paper_2307_10479_gb300 as deg
+    from paper_2307_10479_gb300 import graphs
+    w = synth.WORKLOADS[args.stop_sweep]
+    w = synth.scaled(w, args.n, w.nq) if args.n else w
+    base, q = w.base(), w.queries()
+    idx = graphs.load_or_build(w, base, allow_build=False)
+    idx.upload(("f32",))
+    qd = torch.from_numpy(q).cuda()
+    gt = deg.knn_exact(torch.from_numpy(base).cuda(), qd, K)[0].cpu().numpy()
+    stream = torch.cuda.current_stream()
+    form = dict(precision="f32", entry="fixed")
+
+    def run(eps, learned):
+        ids, _, tr = idx.search(qd, k=K, eps=eps, learned_stop=learned, with_trace=True, **form)
+        return recall(ids.cpu().numpy(), gt), float(tr[:, 1].float().mean()), float(tr[:, 0].float().mean())
+
+    def timed(eps, learned):
+        ms = time_steps(lambda: idx.search(qd, k=K, eps=eps, learned_stop=learned, **form), 10, 3, stream)
+        return len(q) / (statistics.mean(ms) / 1e3)
+
+    eps0, _ = pick_eps(idx, qd, gt, **form)
+    # the grid is coarse above 0.1: bisect down to 0.001 between the last miss and the first hit
+    below = [e for e in EPS_GRID if e < eps0]
+    lo, hi = (below[-1] if below else 0.0), eps0
+    while hi - lo > 0.0011:
+        mid = round((lo + hi) / 2, 4)
+        if run(mid, False)[0] >= TARGET_RECALL:
+            hi = mid
+        else:
+            lo = mid
+    eps0 = hi
+    r0, e0, h0 = run(eps0, False)
+    plain = {"eps": eps0, "recall_at_10": r0, "E_mean": e0, "H_mean": h0, "qps": timed(eps0, False)}
+    log(f"[stop] plain eps {eps0}: recall {r0:.4f}, E {e0:.0f}, {plain['qps']:.0f} QPS")
+    tq = torch.from_numpy(w.training_queries(20000)).cuda()
+    cap = 1024
+    feats, labels, counts = idx.stop_record(tq, k=K, eps=eps0, cap=cap, **form)
+    mask = torch.arange(cap, device="cuda")[None, :] < counts[:, None]
+    wts, hist = deg.train_stop_model(feats[mask].contiguous(), labels[mask].contiguous(), epochs=4, batch=8192)
+    samples = int(mask.sum())
+    del feats, labels, counts, mask, tq
+    log(f"[stop] trained on {samples} hops, loss {[round(h, 4) for h in hist]}")
+    grid = [eps0] + [e for e in EPS_GRID if e > eps0][:7]
+    points = []
+    for th in (0.5, 0.6, 0.7, 0.8, 0.9):
+        idx.set_stop_model(wts, th)
+        for eps in grid:
+            r, e, h = run(eps, True)
+            points.append({"threshold": th, "eps": eps, "recall_at_10": r, "E_mean": e, "H_mean": h})
+            if r >= TARGET_RECALL:
+                break                                  # larger eps only costs more at this threshold
+    ok = [p for p in points if p["recall_at_10"] >= TARGET_RECALL]
+    best = None
+    for p in sorted(ok, key=lambda p: p["E_mean"])[:3]:
+        idx.set_stop_model(wts, p["threshold"])
+        p["qps"] = timed(p["eps"], True)
+        if best is None or p["qps"] > best["qps"]:
+            best = p
+    line = {"stop_sweep": w.name, "n": w.n, "dim": w.dim, "queries": len(q), "k": K, "form": "float32, fixed entry",
+            "target_recall": TARGET_RECALL, "plain": plain, "learned": best, "train_hops": samples,
+            "loss": [round(h, 4) for h in hist], "points": points,
+            "qps_ratio": best["qps"] / plain["qps"] if best else None,
+            "evals_ratio": best["E_mean"] / plain["E_mean"] if best else None}
+    print(json.dumps(line), flush=True)
+
+
 SERVE_RATES = (50_000, 100_000, 200_000, 500_000)
 SERVE_REQUESTS = 100_000
 
@@ -329,12 +402,18 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")
+    ap.add_argument("--stop-sweep", default=None, metavar="WORKLOAD",
+                    help="learned stop against the plain eps rule on this workload (needs its graph file)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.stop_sweep:
+        if rank == 0:
+            run_stop_sweep(args)
         return
 
     import torch

@@ -145,6 +145,18 @@ def algorithmic_bytes(trace, dim, degree, k, row_bytes):
     return int((dim * 4 + H * degree * 4 + E * row_bytes + k * 8).sum())
 
 
+def bisect_eps(lo, hi, reaches, tol=0.001):
+    """Smallest eps (to tol) reaching the recall target, given a miss at lo and a hit at hi and a
+    predicate reaches(eps) that is monotone in eps (a larger eps only widens the search)."""
+    while hi - lo > tol * 1.1:
+        mid = round((lo + hi) / 2, 4)
+        if reaches(mid):
+            hi = mid
+        else:
+            lo = mid
+    return hi
+
+
 def pick_eps(idx, qd, gt, **form):
     """Smallest eps of the grid whose recall@10 reaches the target, for one search form."""
     import torch
@@ -281,14 +293,7 @@ def run_stop_sweep(args):
     eps0, _ = pick_eps(idx, qd, gt, **form)
     # the grid is coarse above 0.1: bisect down to 0.001 between the last miss and the first hit
     below = [e for e in EPS_GRID if e < eps0]
-    lo, hi = (below[-1] if below else 0.0), eps0
-    while hi - lo > 0.0011:
-        mid = round((lo + hi) / 2, 4)
-        if run(mid, False)[0] >= TARGET_RECALL:
-            hi = mid
-        else:
-            lo = mid
-    eps0 = hi
+    eps0 = bisect_eps(below[-1] if below else 0.0, eps0, lambda e: run(e, False)[0] >= TARGET_RECALL)
     r0, e0, h0 = run(eps0, False)
     plain = {"eps": eps0, "recall_at_10": r0, "E_mean": e0, "H_mean": h0, "qps": timed(eps0, False)}
     log(f"[stop] plain eps {eps0}: recall {r0:.4f}, E {e0:.0f}, {plain['qps']:.0f} QPS")

@@ -65,7 +65,7 @@ def source_digest():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel, eps):
+def recorded_traffic(kernel, eps, workload=WORKLOAD):
     """DRAM bytes per launch of a search kernel ("fp8" headline form, "plain" float32 form) from
     the last ncu capture summarised in profiles/, if the sources are unchanged since and the
     capture ran at the same eps (else null)."""
@@ -75,7 +75,7 @@ def recorded_traffic(kernel, eps):
             if ":" in line and not line.startswith("#"):
                 key, val = line.split(":", 1)
                 kv[key.strip()] = val.strip()
-        if (kv.get("source_digest") == source_digest() and kv.get("workload") == WORKLOAD
+        if (kv.get("source_digest") == source_digest() and kv.get("workload") == workload
                 and abs(float(kv[f"eps_{kernel}"]) - eps) < 1e-9):
             return int(kv[f"dram_bytes_per_launch_{kernel}"])
     except Exception:
@@ -172,13 +172,26 @@ def pick_eps(idx, qd, gt, **form):
 
 # Search forms measured: the paper's plain search (float32 rows, fixed entry vertex) and the
 # library's fast forms (entry routed to the nearest pivot; reduced-precision rows + re-rank).
-FORMS = {
-    "plain float32, fixed entry": dict(precision="f32", entry="fixed"),
-    "float32, pivot entry": dict(precision="f32", entry="pivot"),
-    "bf16 + re-rank 32, pivot entry": dict(precision="bf16", rerank=32, entry="pivot"),
-    "fp8 + re-rank 32, pivot entry": dict(precision="fp8", rerank=32, entry="pivot"),
-}
-ROW_BYTES = {"f32": 512, "bf16": 256, "fp8": 128 + 4}
+def make_forms(rerank=32):
+    return {
+        "plain float32, fixed entry": dict(precision="f32", entry="fixed"),
+        "float32, pivot entry": dict(precision="f32", entry="pivot"),
+        f"bf16 + re-rank {rerank}, pivot entry": dict(precision="bf16", rerank=rerank, entry="pivot"),
+        f"fp8 + re-rank {rerank}, pivot entry": dict(precision="fp8", rerank=rerank, entry="pivot"),
+    }
+
+
+FORMS = make_forms()
+
+
+def row_bytes(precision, dim):
+    """Algorithmic bytes of one row in a storage: float32, bf16, or FP8 codes + a float32 scale
+    (rows padded to 16-byte chunks, as stored)."""
+    if precision == "f32":
+        return 4 * ((dim + 3) // 4 * 4)
+    if precision == "bf16":
+        return 2 * ((dim + 7) // 8 * 8)
+    return (dim + 15) // 16 * 16 + 4
 
 
 def time_steps(fn, steps, warmup, stream):
@@ -225,7 +238,7 @@ def read_adjacency(path):
 
 
 def workload(args):
-    w = synth.WORKLOADS[WORKLOAD]
+    w = synth.WORKLOADS[getattr(args, "workload", WORKLOAD)]
     return synth.scaled(w, args.n, w.nq) if args.n else w
 
 
@@ -407,9 +420,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
+                    help="workload of the form table (the headline is the default)")
+    ap.add_argument("--rerank", type=int, default=32, help="re-rank width of the reduced-precision forms")
     ap.add_argument("--stop-sweep", default=None, metavar="WORKLOAD",
                     help="learned stop against the plain eps rule on this workload (needs its graph file)")
     args = ap.parse_args()
+    global FORMS
+    FORMS = make_forms(args.rerank)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -465,7 +483,7 @@ def main():
         _, _, st, tr = idx.search(qd, k=K, eps=eps, with_status=True, with_trace=True, **form)
         trace = tr.cpu().numpy()
         assert (st.cpu().numpy() == 0).all()
-        rb = ROW_BYTES[form.get("precision", "f32")]
+        rb = row_bytes(form.get("precision", "f32"), dim)
         alg = algorithmic_bytes(trace, dim, degree, K, rb)
         if form.get("rerank"):
             alg += len(q) * form["rerank"] * dim * 4          # re-rank reads float32 rows
@@ -494,7 +512,7 @@ def main():
         forms[name], _ = measure(name, FORMS[name], max(3, args.steps // 4), args.warmup)
     # learned early stop: trained (untimed) with the library's kernels on traces of 50,000 held-out
     # queries of the fp8 / pivot-entry form, then measured like the other forms
-    base_name = "fp8 + re-rank 32, pivot entry"
+    base_name = f"fp8 + re-rank {args.rerank}, pivot entry"
     t_eps = forms[base_name]["eps"] + 0.01
     tq = torch.from_numpy(w.training_queries(50000)).cuda()
     feats, labels, counts = idx.stop_record(tq, k=K, eps=t_eps, cap=512, **FORMS[base_name])
@@ -535,23 +553,28 @@ def main():
                 "per_query": {"H_mean": r["H_mean"], "H_max": r["H_max"], "E_mean": r["E_mean"],
                               "second_kernel_frac": r["second_kernel_frac"]}}
 
+    rows_mb = n * row_bytes("f32", dim) / 1e6
+    graph_mb = n * ((degree + 3) // 4 * 4) * 4 / 1e6
+    l2_note = (f"index {rows_mb:.0f} MB rows + {graph_mb:.0f} MB graph "
+               f"{'>' if rows_mb + graph_mb > 129 else '<='} 129 MB L2; no flush")
     kname = {"f32": "F32Rows, 32 lanes/row", "bf16": "BF16Rows, 16 lanes/row", "fp8": "FP8Rows, 8 lanes/row"}
     line = {
-        "metric": METRIC, "value": head["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if w.name == WORKLOAD else METRIC.replace("(1M x 128)", f"({n} x {dim})"),
+        "value": head["qps"], "unit": "queries/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if FORMS[best]["precision"] == "f32" else FORMS[best]["precision"],
         "data": "synthetic",
         "config": {"workload": w.name, "n": n, "dim": dim, "degree": degree, "queries_per_step": len(q), "k": K,
                    "eps": eps, "recall_at_10": head["recall_at_10"], "form": best,
-                   "parallelism": f"replicas x{world}", "l2": "index 512 MB rows + 128 MB graph > 129 MB L2; no flush"},
+                   "parallelism": f"replicas x{world}", "l2": l2_note},
         "latency_ms": {"p50": head["p50_ms"], "p99": head["p99_ms"], "what": "whole 10k-query batch per step"},
         "hbm_gbs": head["achieved_gbs"],
         "vs_plain_fp32": head["qps"] / plain["qps"],
         "forms": forms,
         "roofline": roofline(head, f"search_fast_kernel ({kname[FORMS[best]['precision']]})",
-                             recorded_traffic("fp8", eps) if FORMS[best]["precision"] == "fp8" else None),
+                             recorded_traffic("fp8", eps, w.name) if FORMS[best]["precision"] == "fp8" else None),
         "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)",
-                                        recorded_traffic("plain", plain["eps"])),
+                                        recorded_traffic("plain", plain["eps"], w.name)),
         "knn_exact": knn_line(knn_ms, len(q), n, dim),
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},

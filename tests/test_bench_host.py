@@ -57,3 +57,18 @@ def test_recorded_traffic_only_for_the_same_sources_and_eps(tmp_path, monkeypatc
     f.unlink()
     assert bench.recorded_traffic("fp8", 0.003) is None      # no capture
 
+
+
+def test_row_bytes_match_the_stored_layouts():
+    # float32 rows padded to 4 floats, bf16 to 8 values, FP8 codes to 16 bytes plus a float32 scale
+    assert [bench.row_bytes(p, 128) for p in ("f32", "bf16", "fp8")] == [512, 256, 132]
+    assert [bench.row_bytes(p, 100) for p in ("f32", "bf16", "fp8")] == [400, 208, 116]
+    assert [bench.row_bytes(p, 960) for p in ("f32", "bf16", "fp8")] == [3840, 1920, 964]
+
+
+def test_default_forms_are_the_headline_forms():
+    f = bench.make_forms()
+    assert list(f) == ["plain float32, fixed entry", "float32, pivot entry", "bf16 + re-rank 32, pivot entry",
+                       "fp8 + re-rank 32, pivot entry"]
+    assert f["fp8 + re-rank 32, pivot entry"] == dict(precision="fp8", rerank=32, entry="pivot")
+    assert "fp8 + re-rank 64, pivot entry" in bench.make_forms(64)

@@ -617,7 +617,7 @@ cudaError_t host_alloc(T** p, size_t count) {
 template <class T>
 T* dev_view(T* host) {
     void* d = nullptr;
-    cudaHostGetDevicePointer(&d, host, 0);
+    if (cudaHostGetDevicePointer(&d, host, 0) != cudaSuccess) return nullptr;   // caller checks
     return static_cast<T*>(d);
 }
 
@@ -665,6 +665,10 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
                 dev_view(s->status), dev_view(s->trace), dev_view(s->done), dev_view(s->tail), dev_view(s->stop),
                 s->kstatus, s->claim, s->cap, s->kmax, cfg->entry_mode, cfg->precision, cfg->rerank,
                 cfg->learned_stop ? 1 : 0, (unsigned long long)(cfg->idle_timeout_s * 1e9)};
+    if (!a.vecs || !a.meta || !a.ids || !a.dists || !a.status || !a.trace || !a.done || !a.tail || !a.stop) {
+        server_free(s);
+        return fail(DEG_ECUDA, "serve_start: no device view of the mapped ring");
+    }
     if (launch_serving(a, idx->ws, reinterpret_cast<deg_stream_t>(s->stream), &s->warps, &why) != 0) {
         server_free(s);
         return fail(DEG_ECUDA, "serve_start: " + why);

@@ -101,8 +101,11 @@ int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why)
         return (int)e;
     }
     const int tb = 128, jb = (dim + tb - 1) / tb;
-    cudaMemsetAsync(hist, 0, 4ll * 256 * dim, st);
-    cudaMemsetAsync(best, 0xff, 8, st);
+    if ((e = cudaMemsetAsync(hist, 0, 4ll * 256 * dim, st)) != cudaSuccess || (e = cudaMemsetAsync(best, 0xff, 8, st)) != cudaSuccess) {
+        cudaFree(prefix); cudaFree(rank); cudaFree(hist); cudaFree(best);
+        *why = cudaGetErrorString(e);
+        return (int)e;
+    }
     median_init_kernel<<<jb, tb, 0, st>>>(dim, (uint32_t)((ix.n - 1) / 2), prefix, rank);
     const dim3 hg(dim, (unsigned)((ix.n + kRowsPerBlock - 1) / kRowsPerBlock));
     for (int pass = 0; pass < 4; ++pass) {

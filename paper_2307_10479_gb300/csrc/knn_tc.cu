@@ -817,8 +817,8 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     if (!make_map(&tq, qb, nq, kpad, 2ull * kpad, TM) || !make_map(&tx_all, xb, n, kpad, 2ull * kpad, TN) ||
         !make_map(&tx_sample, xb, ns, kpad, 2ull * kpad * stride, TN))
         return *why = "tensor map encoding failed", (int)cudaErrorInvalidValue;
-    if ((e = cudaMemsetAsync(maxima, 0, 16, st)) != cudaSuccess || (e = cudaMemsetAsync(xn, 0, 4ull * tiles_n * TN, st)) != cudaSuccess)
-        return *why = cudaGetErrorString(e), (int)e;
+    cudaMemsetAsync(maxima, 0, 16, st);
+    cudaMemsetAsync(xn, 0, 4ull * tiles_n * TN, st);
     bf16_rows_kernel<<<2048, 256, 0, st>>>(base, n, dim, kpad, xb, xn, xr);
     bf16_rows_kernel<<<1024, 256, 0, st>>>(queries, nq, dim, kpad, qb, qn, qr);
     row_maxima_kernel<<<304, 256, 0, st>>>(xn, xr, n, maxima);
@@ -829,8 +829,8 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
         auto grid = [&](int64_t tiles) { return (unsigned)std::min<int64_t>((int64_t)qblocks * tiles, sms); };
         const TcArgs sa{(int32_t)q0, (int32_t)qc, qblocks, ns, tiles_s, kpad / KC, qn + q0, xs, gmin, nullptr, nullptr, nullptr, 0, err};
         const TcArgs fa{(int32_t)q0, (int32_t)qc, qblocks, n, tiles_n, kpad / KC, qn + q0, xn, nullptr, limit, cand, cnt, cap, err};
-        if ((e = cudaMemsetAsync(ov, 0, 4ull * (chunk + 2), st)) != cudaSuccess || (e = cudaMemsetAsync(cnt, 0, 4ull * qc, st)) != cudaSuccess)
-            break;
+        cudaMemsetAsync(ov, 0, 4ull * (chunk + 2), st);
+        cudaMemsetAsync(cnt, 0, 4ull * qc, st);
         dist_tc_kernel<false><<<grid(tiles_s), kTcThreads, kSmemDyn, st>>>(tq, tx_sample, sa);
         sample_limit_kernel<<<(unsigned)qc, kSelThreads, 0, st>>>(gmin, (int)ng, k, qn + q0, qr + q0, maxima, kpad, limit);
         dist_tc_kernel<true><<<grid(tiles_n), kTcThreads, kSmemDyn, st>>>(tq, tx_all, fa);
@@ -938,10 +938,8 @@ int knn_plan_create(KnnPlan** out, const float* rows, int64_t row_stride, const 
         knn_plan_destroy(p);
         return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
     }
-    if ((e = cudaMemsetAsync(p->xn, 0, 4ull * p->tiles * TN, st)) != cudaSuccess || (e = cudaMemsetAsync(p->maxima, 0, 16, st)) != cudaSuccess) {
-        knn_plan_destroy(p);
-        return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
-    }
+    cudaMemsetAsync(p->xn, 0, 4ull * p->tiles * TN, st);
+    cudaMemsetAsync(p->maxima, 0, 16, st);
     gather_plan_rows_kernel<<<256, 256, 0, st>>>(rows, row_stride, row_ids, n, dim, p->x32);
     bf16_rows_kernel<<<256, 256, 0, st>>>(p->x32, n, dim, p->kpad, p->xb, p->xn, p->xr);
     row_maxima_kernel<<<64, 256, 0, st>>>(p->xn, p->xr, n, p->maxima);
@@ -982,8 +980,8 @@ int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, flo
         return *why = "knn plan: tensor map encoding failed", (int)cudaErrorInvalidValue;
     const int32_t qblocks = (int32_t)((nq + TM - 1) / TM);
     const unsigned grid = (unsigned)std::min<int64_t>((int64_t)qblocks * p->tiles, p->sms);
-    if ((e = cudaMemsetAsync(p->flags, 0, 16, st)) != cudaSuccess || (e = cudaMemsetAsync(p->cnt, 0, 4ull * nq, st)) != cudaSuccess)
-        return *why = cudaGetErrorString(e), (int)e;
+    cudaMemsetAsync(p->flags, 0, 16, st);
+    cudaMemsetAsync(p->cnt, 0, 4ull * nq, st);
     bf16_rows_kernel<<<256, 256, 0, st>>>(queries, nq, p->dim, p->kpad, p->qb, p->qn, p->qr);
     const TcArgs sa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, p->gmin, nullptr, nullptr, nullptr, 0,
                     p->flags};

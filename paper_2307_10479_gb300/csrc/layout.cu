@@ -272,8 +272,7 @@ int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int
     // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
     if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, dists, stream, why)) return r;
     if (order) {
-        const cudaError_t m = cudaMemsetAsync(cursors, 0, 2 * sizeof(int32_t), st);
-        if (m != cudaSuccess) return *why = cudaGetErrorString(m), (int)m;
+        cudaMemsetAsync(cursors, 0, 2 * sizeof(int32_t), st);
         route_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, dists, (int32_t)nq, ix.pivots, ix.far_tau,
                                                                      seeds, order, cursors);
     } else {

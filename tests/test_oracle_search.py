@@ -221,3 +221,55 @@ def test_median_vertex_matches_numpy_definition():
     med = np.sort(base, axis=0)[(1001 - 1) // 2].astype(np.float64)
     d = np.sqrt(((base.astype(np.float64) - med) ** 2).sum(1))
     assert oracle.median_vertex(base) == int(np.argmin(d))
+
+
+# ----------------------------------------------------------------------------------------------
+# Alg. 1 on reduced-precision rows with a float32 re-rank (the library's bf16/FP8 forms)
+# ----------------------------------------------------------------------------------------------
+
+def test_decoded_search_on_exact_rows_is_the_float32_search(small_deg):
+    # Rows whose values bf16 holds exactly decode to themselves, so with keep = k the
+    # reduced-precision search is Alg. 1 on the float32 rows: same ids, same distances.
+    base, adj = small_deg
+    exact = np.round(base * 64) / 64                          # 6 fractional bits: exact in bf16
+    q = synth.uniform(30, 8, 15)
+    dec = oracle.decode("bf16", oracle.quantize_bf16(exact))
+    assert np.array_equal(dec, exact.astype(np.float64))
+    for eps in (0.0, 0.2):
+        seeds = np.zeros(30, np.int32)
+        ids, d = oracle.range_search_decoded(dec, exact, adj, q, seeds, 10, eps, keep=10)
+        o_ids, o_d, _ = oracle.range_search(exact, adj, q, seeds, 10, eps)
+        assert np.array_equal(ids, o_ids)
+        np.testing.assert_allclose(d, o_d, rtol=1e-14)
+
+
+def test_decoded_search_keeping_everything_reranks_to_exact_knn(small_deg):
+    # With a huge eps every vertex is checked; keeping all n results and re-ranking them on the
+    # float32 rows gives the exact k-NN (Eq. 1) of the float32 rows, although FP8 distances alone
+    # would order them differently.
+    base, adj = small_deg
+    q = synth.uniform(30, 8, 16)
+    dec = oracle.decode("fp8", *oracle.quantize_fp8(base))
+    ids, d = oracle.range_search_decoded(dec, base, adj, q, np.zeros(30, np.int32), 10, 1e9, keep=len(base))
+    gid, gd = oracle.knn_bruteforce(base, q, 10)
+    assert np.array_equal(ids, gid)
+    np.testing.assert_allclose(d, gd, rtol=1e-14)
+    # the FP8 order alone is not the exact one on this data (else the test above proves nothing)
+    fid, _ = oracle.knn_bruteforce(dec.astype(np.float32), q, 10)
+    assert not np.array_equal(fid, gid)
+
+
+def test_decoded_search_returns_the_float32_distances_of_the_kept_candidates(small_deg):
+    # keep > k: the k returned are the k closest by float32 distance among the keep candidates
+    # the decoded search found (with a huge eps these are the decoded rows' keep nearest).
+    base, adj = small_deg
+    q = synth.uniform(20, 8, 17)
+    dec = oracle.decode("fp8", *oracle.quantize_fp8(base))
+    keep = 32
+    ids, d = oracle.range_search_decoded(dec, base, adj, q, np.zeros(20, np.int32), 10, 1e9, keep=keep)
+    cand = np.argsort(((dec[None, :, :] - q[:, None, :].astype(np.float64)) ** 2).sum(-1), axis=1, kind="stable")[:, :keep]
+    for i in range(len(q)):
+        true = np.sqrt(((base[cand[i]].astype(np.float64) - q[i].astype(np.float64)) ** 2).sum(-1))
+        order = np.lexsort((cand[i], true))[:10]
+        assert np.array_equal(ids[i], cand[i][order])
+        np.testing.assert_allclose(d[i], true[order], rtol=1e-14)

@@ -40,7 +40,9 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            L = ctypes.CDLL(build())
+            # DEG_ORACLE_LIB names another build of these sources (the mutation tests load copies
+            # with one planted mistake this way)
+            L = ctypes.CDLL(os.environ.get("DEG_ORACLE_LIB") or build())
             P, i32, i64, f64, u64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_uint64
             L.oracle_knn_bruteforce.argtypes = [P, i64, i32, P, i64, i32, P, P, P, i32]
             L.oracle_knn_bruteforce.restype = ctypes.c_int

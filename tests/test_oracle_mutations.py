@@ -41,6 +41,17 @@ MUTATIONS = {
                            "(void)base;", "test_oracle_search.py"),
     "first ReLU dropped": ("oracle_mlp.cpp", "            h1[j] = a > 0 ? a : 0;", "            h1[j] = a;",
                            "test_oracle_mlp.py", 2),                 # the loss and the prediction paths
+    "squared distance": ("oracle_search.cpp", "        s += t * t;\n    }\n    return std::sqrt(s);",
+                         "        s += t * t;\n    }\n    return s;", "test_oracle_search.py"),
+    "upper median": ("oracle_search.cpp", "med[j] = col[(n - 1) / 2];", "med[j] = col[n / 2];",
+                     "test_oracle_search.py"),
+    "median vertex ties to the higher id": ("oracle_search.cpp", "if (d < best_d) { best_d = d; best = (int32_t)i; }",
+                                            "if (d <= best_d) { best_d = d; best = (int32_t)i; }", "test_oracle_search.py"),
+    "FP8 scale for the wrong maximum": ("oracle_quant.cpp", "m > 0.f ? m / 448.0f : 1.0f", "m > 0.f ? m / 240.0f : 1.0f",
+                                        "test_oracle_quant.py"),
+    "bf16 truncates": ("oracle_quant.cpp", "    u += 0x7fffu + lsb;", "    u += 0u * lsb;", "test_oracle_quant.py"),
+    "E4M3 subnormal boundary": ("oracle_quant.cpp", "e < -6 ? std::ldexp(1.0, -9)", "e < -7 ? std::ldexp(1.0, -9)",
+                                "test_oracle_quant.py"),
 }
 
 
@@ -71,7 +82,7 @@ def _run_pins(lib_path, pin_file):
 def test_unmodified_copy_passes_the_pins(objects, tmp_path):
     lib = tmp_path / "liboracle.so"
     _link(objects, lib)
-    for pin_file in ("test_oracle_search.py", "test_oracle_mlp.py"):
+    for pin_file in ("test_oracle_search.py", "test_oracle_mlp.py", "test_oracle_quant.py"):
         r = _run_pins(lib, pin_file)
         assert r.returncode == 0, r.stdout[-2000:]
 

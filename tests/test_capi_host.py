@@ -113,3 +113,15 @@ def test_knn_exact_argument_checks(L):
     assert L.knn_exact(ctypes.c_void_p(16), 10, ctypes.c_void_p(16), 1, 4, 0, ctypes.c_void_p(16),
                        ctypes.c_void_p(16), None) == deg.DEG_EINVAL
     assert b"k must be" in L.deg_last_error()
+
+
+@pytest.mark.parametrize("n,dim,d,seed", [(300, 8, 8, 5), (500, 6, 4, 6), (400, 12, 10, 7)])
+def test_library_builder_equals_the_oracle_on_integer_rows(L, n, dim, d, seed):
+    # Two independent implementations of Alg. 2-5 with the same readings: the library's in float32,
+    # the oracle's in FP64. On small integer coordinates every squared distance is exact in both and
+    # distinct distances stay distinct after the square root, so every decision agrees and the
+    # graphs must be identical, edge for edge.
+    base = np.random.default_rng(seed).integers(0, 16, (n, dim)).astype(np.float32)
+    a = oracle.build_graph(base, d, 2 * d, 0.2, d, 0.001, 5)
+    b = deg.Index.build(base, d, 2 * d, 0.2, d, 0.001, 5).adjacency()
+    assert np.array_equal(np.sort(a, axis=1), np.sort(b, axis=1))

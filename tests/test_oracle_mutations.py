@@ -52,6 +52,13 @@ MUTATIONS = {
     "bf16 truncates": ("oracle_quant.cpp", "    u += 0x7fffu + lsb;", "    u += 0u * lsb;", "test_oracle_quant.py"),
     "E4M3 subnormal boundary": ("oracle_quant.cpp", "e < -6 ? std::ldexp(1.0, -9)", "e < -7 ? std::ldexp(1.0, -9)",
                                 "test_oracle_quant.py"),
+    "checkMRNG against the shorter edge": ("oracle_build.cpp", "if (w12 > std::max(weight(v1, u), weight(v2, u))) return false;",
+                                           "if (w12 > std::min(weight(v1, u), weight(v2, u))) return false;",
+                                           "test_oracle_build.py"),
+    "edge swap gain with the wrong sign": ("oracle_build.cpp", "const double g2 = gain - delta(s, v2) + weight(s, nb);",
+                                           "const double g2 = gain + delta(s, v2) - weight(s, nb);", "test_oracle_build.py"),
+    "insertion skips the RNG check": ("oracle_build.cpp", "if (!skip_rng && !check_mrng_tentative(v, b, U)) continue;",
+                                      "if (false) continue;", "test_capi_host.py"),
 }
 
 
@@ -82,7 +89,8 @@ def _run_pins(lib_path, pin_file):
 def test_unmodified_copy_passes_the_pins(objects, tmp_path):
     lib = tmp_path / "liboracle.so"
     _link(objects, lib)
-    for pin_file in ("test_oracle_search.py", "test_oracle_mlp.py", "test_oracle_quant.py"):
+    for pin_file in ("test_oracle_search.py", "test_oracle_mlp.py", "test_oracle_quant.py", "test_oracle_build.py",
+                     "test_capi_host.py"):
         r = _run_pins(lib, pin_file)
         assert r.returncode == 0, r.stdout[-2000:]
 

@@ -59,7 +59,15 @@ MUTATIONS = {
                                            "const double g2 = gain + delta(s, v2) - weight(s, nb);", "test_oracle_build.py"),
     "insertion skips the RNG check": ("oracle_build.cpp", "if (!skip_rng && !check_mrng_tentative(v, b, U)) continue;",
                                       "if (false) continue;", "test_capi_host.py"),
+    "case b tests S1 twice": ("oracle_build.cpp", "for (const Cand& c : S4) path |= (c.id == v4);",
+                              "for (const Cand& c : S1) path |= (c.id == v1);", "test_capi_host.py"),
+    "longest edge ties to the higher id": ("oracle_build.cpp", "(w == wn && c < n)", "(w == wn && c > n)",
+                                           "test_capi_host.py"),
+    "one edge-swap iteration too many": ("oracle_build.cpp", "for (int it = 0; it < i_opt; ++it)",
+                                         "for (int it = 0; it <= i_opt; ++it)", "test_capi_host.py"),
 }
+# Not listed: case a accepting a zero gain (">= 0" for "> 0") changes nothing unless the gain, a sum
+# of square-root distances, is exactly zero, which non-degenerate data never gives.
 
 
 @pytest.fixture(scope="module")

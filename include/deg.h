@@ -2,10 +2,10 @@
  *
  * The paper (arXiv 2307.10479) defines the method:
  *   - Alg. 1 RangeSearch(G, S, q, k, eps) (Sec. 2.1)      -> deg_search / deg_explore
- *   - exploration queries seeded at the query's own vertex (Sec. 5.7) -> deg_explore
+ *   - exploration queries seeded at the query's own vertex (Sec. 6.7) -> deg_explore
  *   - Eq. 1, the exact k nearest neighbours                -> knn_exact
- *   - Sec. 4 construction (Alg. 2-5)                       -> deg_build (host, not the GPU path)
- *   - Sec. 4.4: search graphs drop edge weights and start at the "median vertex"
+ *   - Sec. 5 construction (Alg. 2-5)                       -> deg_build (host, not the GPU path)
+ *   - Sec. 5.4: search graphs drop edge weights and start at the "median vertex"
  *                                                          -> deg_upload / deg_entry_vertex
  *
  * Conventions for every call:
@@ -75,7 +75,7 @@ typedef struct deg_index deg_index;   /* opaque, owned by the library */
 
 /* ---- index lifecycle ------------------------------------------------------------------- */
 
-/* Build a DEG over base_host [n][dim] float32 on the host (paper Sec. 4.2-4.3, Alg. 2-5).
+/* Build a DEG over base_host [n][dim] float32 on the host (paper Sec. 5.2-5.3, Alg. 2-5).
  * Copies the vectors. n >= degree + 1. Single-threaded; minutes to hours at n = 10^6.
  * progress (nullable) receives the number of vertices inserted so far. */
 DEG_API deg_status deg_build(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
@@ -88,7 +88,7 @@ DEG_API deg_status deg_index_from_arrays(const float* base_host, const int32_t* 
                                  int32_t dim, int32_t degree, deg_index** out);
 
 /* Graph file: header, adjacency [n][degree] int32 and, if with_vectors, the vectors. Edge
- * weights are not stored (Sec. 4.4: search drops them; they are recomputed when needed).
+ * weights are not stored (Sec. 5.4: search drops them; they are recomputed when needed).
  * A file without vectors carries a checksum of them; deg_load then requires base_host
  * (otherwise ignored, may be NULL) and fails with DEG_EIO if the checksum differs. */
 DEG_API deg_status deg_save(const deg_index* idx, const char* path, int32_t with_vectors);
@@ -102,7 +102,7 @@ DEG_API deg_status deg_get_adjacency(const deg_index* idx, int32_t* adj_host);
  * multiple of 4 floats), the adjacency, and the reduced-precision copies named in
  * precision_mask (bit 1 << DEG_BF16, bit 1 << DEG_FP8). Computes the fixed entry vertex on the
  * device: the row nearest to the per-coordinate lower median (rank floor((n-1)/2)) of all rows
- * -- the paper's "median vertex" (Sec. 4.4). Synchronises `stream` before returning. */
+ * -- the paper's "median vertex" (Sec. 5.4). Synchronises `stream` before returning. */
 DEG_API deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* stream);
 
 /* Copy the device's reduced-precision rows out to the host, unpadded: precision DEG_BF16 ->
@@ -131,7 +131,7 @@ typedef struct {
                              main kernel, 0 = 32768 (the maximum); a query needing more is
                              finished by a second kernel with room for all n vertices          */
     int32_t entry_mode;   /* plain searches with no seeds: 0 = the fixed entry vertex (paper,
-                             Sec. 4.4); 1 = per query, the nearest of the index's pivot vertices
+                             Sec. 5.4); 1 = per query, the nearest of the index's pivot vertices
                              (about n/256, at most 4096, chosen at upload) -- not in the paper */
     int32_t learned_stop; /* 1: after every hop the index's stop network (deg_set_stop_model)
                              may end the search early; the eps test still applies. Not in the
@@ -148,7 +148,7 @@ DEG_API deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t 
                       const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
                       int32_t* status_dev, void* stream);
 
-/* Exploration (Sec. 5.7): query q is the indexed vertex vertex_ids_dev[q]; the search starts
+/* Exploration (Sec. 6.7): query q is the indexed vertex vertex_ids_dev[q]; the search starts
  * at that vertex and never returns it (the user has already seen it). */
 DEG_API deg_status deg_explore(deg_index* idx, const int32_t* vertex_ids_dev, int64_t nq, int32_t k,
                        float eps, int32_t* ids_dev, float* dists_dev, int32_t* status_dev,

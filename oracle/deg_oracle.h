@@ -35,7 +35,7 @@ int oracle_range_search(const float* base, int64_t n, int32_t dim,
                         int32_t explore, int32_t k, double eps,
                         int32_t* ids, double* dists, int64_t* trace, int32_t nthreads);
 
-/* Fixed entry vertex ("median vertex of the graph", Sec. 4.4): the base row nearest (FP64,
+/* Fixed entry vertex (the median vertex, Sec. 5.4): the base row nearest (FP64,
  * tie -> lower id) to the coordinate-wise lower median of all base rows. */
 int32_t oracle_median_vertex(const float* base, int64_t n, int32_t dim);
 
@@ -47,7 +47,7 @@ int deg_build_oracle(const float* base, int64_t n, int32_t dim, int32_t degree,
                      int32_t i_opt, int32_t refine_rounds, uint64_t seed,
                      int32_t* adj_out, double* weights_out);
 
-/* Structural invariants of a DEG (Sec. 4.1). Returns a bit mask of violations:
+/* Structural invariants of a DEG (Sec. 5.1). Returns a bit mask of violations:
  *  1 degree slot empty/out of range, 2 self loop, 4 duplicate edge, 8 asymmetric,
  *  16 disconnected (BFS), 32 odd or < 4 degree, 64 has a bridge (only tested if n <= bridge_max_n). */
 int32_t oracle_check_graph(const int32_t* adj, int64_t n, int32_t degree, int64_t bridge_max_n);

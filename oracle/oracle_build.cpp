@@ -1,11 +1,11 @@
 // CPU oracle (test infrastructure only): DEG construction -- checkMRNG (Alg. 2),
 // ExtendGraph (Alg. 3, scheme C with RNG checks), optimizeEdge (Alg. 4, scheme D gain) and
-// dynamicEdgeOptimization (Alg. 5) -- plus the structural invariants of Sec. 4.1, AND (Eq. 4)
+// dynamicEdgeOptimization (Alg. 5) -- plus the structural invariants of Sec. 5.1, AND (Eq. 4)
 // and GQ (Eq. 3). FP64 distances and stored FP64 edge weights w(u,v) = delta(u,v).
 //
 // Readings where the algorithms are silent or garbled:
 //  B1 insertion order = vertex id; the start graph is K_{d+1} on ids 0..d; the ExtendGraph
-//     search seed is vertex 0 (Sec. 4.2 step 1 allows any vertex).
+//     search seed is vertex 0 (Sec. 5.2 step 1 allows any vertex).
 //  B2 checkMRNG(G, v, b) inside ExtendGraph treats the tentative set U as N(v) with
 //     w(v,u) = delta(v,u) (v itself has no edges until the end of Alg. 3).
 //  B3 a b already in U, or whose neighbours are all in U, is skipped; n = the neighbour of b
@@ -267,7 +267,7 @@ extern "C" int deg_build_oracle(const float* base, int64_t n, int32_t dim, int32
                                 int32_t k_ext, double eps_ext, int32_t k_opt, double eps_opt,
                                 int32_t i_opt, int32_t refine_rounds, uint64_t seed,
                                 int32_t* adj_out, double* weights_out) {
-    // Even regularity, d >= 4 (Sec. 4.1); the smallest DEG_d is K_{d+1}.
+    // Even regularity, d >= 4 (Sec. 5.1); the smallest DEG_d is K_{d+1}.
     if (!base || !adj_out || dim <= 0 || degree < 4 || degree % 2 || n < degree + 1) return -1;
     if (k_ext < degree || k_opt < 1 || i_opt < 0 || eps_ext < 0 || eps_opt < 0) return -1;
     try {

@@ -1,5 +1,5 @@
 // CPU oracle (test infrastructure only): reduced-precision storage of the base rows and the
-// search over it. The paper stores float32 features only (Sec. 4.4); the BF16 and FP8 stores
+// search over it. The paper stores float32 features only (Sec. 5.4); the BF16 and FP8 stores
 // with a float32 re-rank are the library's extension, so these functions follow the format
 // definitions rather than a passage of the paper:
 //   bfloat16: the upper 16 bits of the float32 pattern, rounded to nearest, ties to even.

@@ -1,5 +1,5 @@
 // CPU oracle (test infrastructure only): exact kNN (Eq. 1), RangeSearch (Alg. 1) and the fixed
-// entry vertex (Sec. 4.4), all in FP64. Deliberately plain: std::set for the candidate and
+// entry vertex (Sec. 5.4), all in FP64. Deliberately plain: std::set for the candidate and
 // result sets, std::unordered_set for the checked set, no blocking, no fusion.
 #include "deg_oracle.h"
 #include "oracle_common.h"
@@ -42,7 +42,7 @@ void parallel_for(int64_t count, int nthreads, const std::function<void(int64_t)
 // Alg. 1 RangeSearch(G, S, q, k, eps), with the readings:
 //  * C starts as the seed set (seeds count as checked);
 //  * plain search: R starts as the seeds; exploration: seeds are searched from but never
-//    returned (the paper avoids showing a user the item they came from, Sec. 5.7);
+//    returned (the paper avoids showing a user the item they came from, Sec. 6.7);
 //  * r stays +inf until R first exceeds k and is trimmed; r is only updated on a trim;
 //  * argmin over S and argmax over R order by the key (distance, id), lower id first.
 std::vector<Cand> range_search(const Graph& g,
@@ -165,7 +165,7 @@ extern "C" int oracle_range_search(const float* base, int64_t n, int32_t dim,
 }
 
 extern "C" int32_t oracle_median_vertex(const float* base, int64_t n, int32_t dim) {
-    // Sec. 4.4 names "the median vertex of the graph" as the search seed without defining it.
+    // Sec. 5.4 seeds the search at the graph's median vertex without defining that vertex.
     // Reading: per coordinate take the lower median (the element of rank floor((n-1)/2) in
     // ascending order), then return the base row nearest to that vector (tie -> lower id).
     if (!base || n <= 0 || dim <= 0) return -1;

@@ -1,6 +1,6 @@
 // Native DEG construction for the library (host C++, FP32): the graph the GPU search runs on.
 //
-// Implements Sec. 4.2-4.3 of the paper: vertices are inserted in id order into the complete
+// Implements Sec. 5.2-5.3 of the paper: vertices are inserted in id order into the complete
 // graph K_{d+1} on ids 0..d; each insertion runs ExtendGraph (Alg. 3: a range search for the
 // new vertex, then scheme C -- replace the longest edge (b, n) of the best result b by (v, b),
 // (v, n) -- with the checkMRNG test of Alg. 2 in a first pass and without it in a second), then

@@ -60,7 +60,7 @@ deg_status cuda_fail(cudaError_t e, const char* what) {
     return fail(DEG_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// Graph invariants of Sec. 4.1 that the search relies on (entries in range, no loops, no
+// Graph invariants of Sec. 5.1 that the search relies on (entries in range, no loops, no
 // duplicates, symmetric, even degree >= 4). Connectivity is not required by the search.
 deg_status check_graph(const int32_t* adj, int64_t n, int32_t d) {
     if (d < 4 || d % 2) return fail(DEG_EGRAPH, "degree must be even and >= 4");

@@ -1,4 +1,4 @@
-// Fixed entry vertex of the search (paper Sec. 4.4: "the median vertex of the graph").
+// Fixed entry vertex of the search: the graph's median vertex, which Sec. 5.4 names as the seed.
 // Reading: per coordinate take the lower median -- the element of rank floor((n-1)/2) in
 // ascending order -- and return the row nearest to that vector (float32 squared distance,
 // tie -> lower id). The median is found exactly by an 8-bit-digit radix select on the

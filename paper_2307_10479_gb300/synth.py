@@ -1,6 +1,6 @@
 """Seeded synthetic workloads shaped like the paper's datasets.
 
-The paper evaluates on SIFT1M, GloVe, Audio and Enron (Sec. 5.1, Table 1). Those files are
+The paper evaluates on SIFT1M, GloVe, Audio and Enron (Sec. 6.1, Table 1). Those files are
 not available here, so every input is generated from a fixed seed with the shape and value
 distribution of the workload it stands in for:
 

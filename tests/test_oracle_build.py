@@ -1,4 +1,4 @@
-"""Pins for the CPU oracle's construction side (Sec. 4, Alg. 2-5, Eq. 3-4, App. B): structural
+"""Pins for the CPU oracle's construction side (Sec. 5, Alg. 2-5, Eq. 3-4, App. B): structural
 invariants the paper proves for every DEG, hand-built geometry for the MRNG lune test, closed
 forms for AND and GQ, and the bit-exact revert of a failed edge optimisation."""
 import itertools
@@ -23,7 +23,7 @@ def built(request):
 
 
 def test_build_structural_invariants(built):
-    # Sec. 4.1: even-regular, undirected, no loops; |E| = |V| d / 2; connected (Euler) and
+    # Sec. 5.1: even-regular, undirected, no loops; |E| = |V| d / 2; connected (Euler) and
     # bridge-free (2-edge-connected).
     base, adj, _, d = built
     n = adj.shape[0]
@@ -57,7 +57,7 @@ def test_build_cut_set_lower_bound(built):
 
 
 def test_first_graph_is_complete():
-    # The smallest DEG_d is K_{d+1} (Sec. 4.1).
+    # The smallest DEG_d is K_{d+1} (Sec. 5.1).
     base = synth.uniform(7, 3, 30)
     adj = oracle.build_graph(base, 6, 12, 0.2, 6, 0.001, 5)
     for u in range(7):
@@ -81,7 +81,7 @@ def test_check_graph_flags_plants():
 
 
 def test_check_graph_detects_bridge():
-    # An even-regular graph can have no bridge (Sec. 4.1, Euler), so plant one in a 3-regular
+    # An even-regular graph can have no bridge (Sec. 5.1, Euler), so plant one in a 3-regular
     # graph: two copies of K4 with edge (a,b) subdivided by e, the two e's joined by a bridge.
     one = [[2, 3, 4], [2, 3, 4], [0, 1, 3], [0, 1, 2], [0, 1, 9]]
     two = [[r + 5 if r != 9 else 4 for r in row] for row in one]
@@ -143,7 +143,7 @@ def test_and_closed_form_on_simplex():
 
 
 def test_graph_quality_complete_graph_is_one():
-    # Sec. 4.1: a complete graph has GQ = 1 (every vertex is adjacent to its d nearest).
+    # Sec. 5.1: a complete graph has GQ = 1 (every vertex is adjacent to its d nearest).
     base = synth.uniform(5, 3, 34)
     k5 = np.array([[j for j in range(5) if j != i] for i in range(5)], np.int32)
     knn, _ = oracle.knn_bruteforce(base, base, 4, exclude=np.arange(5, dtype=np.int32))

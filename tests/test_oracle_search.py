@@ -197,7 +197,7 @@ def test_alg1_recall_grows_with_eps(small_deg):
 
 
 # ----------------------------------------------------------------------------------------------
-# Fixed entry vertex (Sec. 4.4 "median vertex"; lower-median reading)
+# Fixed entry vertex (Sec. 5.4 "median vertex"; lower-median reading)
 # ----------------------------------------------------------------------------------------------
 
 def test_median_vertex_hand_examples():

@@ -41,6 +41,12 @@ MUTATIONS = {
                            "(void)base;", "test_oracle_search.py"),
     "first ReLU dropped": ("oracle_mlp.cpp", "            h1[j] = a > 0 ? a : 0;", "            h1[j] = a;",
                            "test_oracle_mlp.py", 2),                 # the loss and the prediction paths
+    "backward pass ignores the second ReLU": ("oracle_mlp.cpp", "            d2[i] = h2[i] > 0 ? g : 0;",
+                                              "            d2[i] = g;", "test_oracle_mlp.py"),
+    "first-layer weight gradient transposed": ("oracle_mlp.cpp",
+                                               "grad[OW1 + j * IN + i] += d1[j] * (double)xs[i];",
+                                               "grad[OW1 + (i * H + j) % (H * IN)] += d1[j] * (double)xs[i];",
+                                               "test_oracle_mlp.py"),
     "squared distance": ("oracle_search.cpp", "        s += t * t;\n    }\n    return std::sqrt(s);",
                          "        s += t * t;\n    }\n    return s;", "test_oracle_search.py"),
     "upper median": ("oracle_search.cpp", "med[j] = col[(n - 1) / 2];", "med[j] = col[n / 2];",

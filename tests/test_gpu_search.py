@@ -165,3 +165,50 @@ def test_pivot_entry_parity(cfg1):
     compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d)
     with pytest.raises(cfg1["deg"].DegError):
         idx.search(cfg1["qd"], k=10, eps=0.1, entry="pivot", seeds=torch.zeros(len(q), dtype=torch.int32, device="cuda"))
+
+
+def _circulant(n, d, seed):
+    """A d-regular undirected graph without loops or duplicates: vertex perm[i] joined to
+    perm[i +- 1 .. d/2] (mod n). Alg. 1 needs no DEG property, only a valid graph."""
+    perm = np.random.default_rng(seed).permutation(n).astype(np.int32)
+    offs = np.concatenate([np.arange(1, d // 2 + 1), -np.arange(1, d // 2 + 1)])
+    adj = np.empty((n, d), np.int32)
+    for i in range(n):
+        adj[perm[i]] = perm[(i + offs) % n]
+    return adj
+
+
+@pytest.mark.parametrize("degree", [64, 128])
+def test_degrees_above_one_warp(degree):
+    # Degree 64 and 128 (the largest the kernels take) read a neighbour list in several 32-lane
+    # chunks and admit a hop's candidates in several batches. With a huge eps every vertex is
+    # checked, so R is the exact k-NN and H = E = n on both sides.
+    import paper_2307_10479_gb300 as deg
+    n = 3000
+    base = synth.uniform(n, 16, 62)
+    adj = _circulant(n, degree, 7)
+    assert oracle.check_graph(adj) == 0
+    idx = deg.Index.from_arrays(base, adj)
+    idx.upload()
+    q = synth.uniform(60, 16, 63)
+    ids, d, st, tr = idx.search(torch.from_numpy(q).cuda(), k=10, eps=1e9, with_status=True, with_trace=True)
+    o_ids, o_d, o_tr = oracle.range_search(base, adj, q, np.full(len(q), oracle.median_vertex(base), np.int32), 10, 1e9)
+    assert (st.cpu().numpy() == 0).all()
+    compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d, min_identical=0.95)
+    assert np.array_equal(tr.cpu().numpy()[:, 1], o_tr[:, 1]) and (o_tr[:, 1] == n).all()
+    assert np.array_equal(tr.cpu().numpy()[:, 0], o_tr[:, 0])
+
+
+def test_largest_k():
+    # k = 1024, the largest the kernels take: a 1024-long R (and re-sorted output) per query.
+    import paper_2307_10479_gb300 as deg
+    n = 3000
+    base = synth.uniform(n, 16, 64)
+    adj = _circulant(n, 32, 8)
+    idx = deg.Index.from_arrays(base, adj)
+    idx.upload()
+    q = synth.uniform(20, 16, 65)
+    ids, d, st = idx.search(torch.from_numpy(q).cuda(), k=1024, eps=1e9, with_status=True)
+    gid, gd = oracle.knn_bruteforce(base, q, 1024)
+    assert (st.cpu().numpy() == 0).all()
+    compare_lists(ids.cpu().numpy(), d.cpu().numpy(), gid, gd, min_identical=0.9)

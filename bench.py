@@ -557,6 +557,7 @@ def main():
         return {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
                 "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
                 "alg_bytes_per_launch": r["alg_bytes"],
+                "timed_over": "the whole search call (entry routing included), not the kernel alone",
                 "per_query": {"H_mean": r["H_mean"], "H_max": r["H_max"], "E_mean": r["E_mean"],
                               "second_kernel_frac": r["second_kernel_frac"]}}
 

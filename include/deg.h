@@ -275,7 +275,9 @@ DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* quer
  * Same arguments, results and errors as knn_exact, except:
  *  - the distances live in one static device array of 32 MiB (8,388,608 float32) held by every
  *    GPU that loads the library until the process exits; n must be at most 8,388,608 (else
- *    DEG_EINVAL) and queries are processed in chunks of 8,388,608 / n;
+ *    DEG_EINVAL) and queries are processed in chunks of 8,388,608 / n (at most 4,194,240);
+ *  - the device address is cached with the id of the CUDA context it was looked up in; a call in
+ *    a new context of the device (after cudaDeviceReset, say) looks it up again;
  *  - the first call on a device looks up that array's device address (cudaGetSymbolAddress, with
  *    the device current) and caches it: make that first call before any stream capture;
  *  - all calls share the array and it keeps the last call's contents; two calls whose work

@@ -37,9 +37,10 @@ struct DeviceIndex {
     float* scale8 = nullptr;  // [n] per-row scale of the E4M3 codes
     float* norm8 = nullptr;   // [n][2] {scale s, s^2 ||decoded codes||^2} per E4M3 row
     int32_t dim_pad8 = 0;     // fp8 row stride (multiple of 16)
-    int32_t* adj = nullptr;   // [n][deg_pad], padded slots = -1 (internal ids)
+    int32_t* adj = nullptr;   // uploaded: [n][deg_pad] caller ids, padded slots -1; after the locality
+                              // layout: [n][deg_pad] int2 {internal id, caller id}, row = caller id
     int32_t entry = -1;       // entry vertex, caller's id
-    // Locality layout: rows and adjacency are stored in internal-id order (layout.cu).
+    // Locality layout: rows are stored in internal-id order (layout.cu).
     int32_t* old2new = nullptr;   // [n] caller id -> internal id
     int32_t* new2old = nullptr;   // [n] internal id -> caller id
     int32_t entry_internal = -1;

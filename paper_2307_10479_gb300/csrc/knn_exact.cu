@@ -131,13 +131,18 @@ __global__ void __launch_bounds__(kSelThreads) select_topk_kernel(const float* _
     }
 }
 
+// Queries per launch of dist_tile_kernel: its grid.y (one block row per kTile queries) is at most
+// 65,535.
+constexpr int64_t kMaxChunkQueries = 65535ll * kTile;
+
 }  // namespace
 
 int launch_knn_simt(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim, int32_t k,
                     int32_t* ids, float* dists, deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (k > n) return *why = "k larger than n", (int)cudaErrorInvalidValue;
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, (int64_t)(2ll << 30) / (4 * n)));
+    // grid.y = ceil(chunk / kTile) must stay within 65,535
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({nq, (int64_t)(2ll << 30) / (4 * n), kMaxChunkQueries}));
     float* D = nullptr;
     // A plain allocation, released before returning (the call is a one-off: ground truth).
     cudaError_t e = cudaMalloc(&D, sizeof(float) * chunk * n);
@@ -161,7 +166,12 @@ int launch_knn_simt(const float* base, int64_t n, const float* queries, int64_t 
 // For callers that cannot allocate device memory during the call. The distance buffer is a
 // file-scope __device__ array (32 MiB), so every GPU that loads the library holds it until the
 // process exits. Host code cannot use the array's name as a device address: the first call on a
-// device looks the address up with cudaGetSymbolAddress (that device current) and caches it.
+// device looks the address up with cudaGetSymbolAddress (that device current) and caches it with
+// the id of the CUDA context it belongs to. A later call in another context of that device (after
+// cudaDeviceReset, say, which unloads the module and frees the array) looks it up again instead
+// of handing the kernels a freed address.
+#include <cuda.h>
+
 #include <mutex>
 
 namespace deg {
@@ -172,7 +182,36 @@ static __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[kMaxDevices] = {};
+struct NoAllocSlot {
+    unsigned long long ctx = 0;                                      // id of the context the address is in
+    float* ptr = nullptr;
+};
+NoAllocSlot g_noalloc_slot[kMaxDevices];
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Id of the calling thread's current context (driver entry points found through the runtime, so
+// the library does not link the driver library); 0 when there is none. Holds g_noalloc_mu.
+unsigned long long current_context_id() {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1{}, q2{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
+                                             cudaEnableDefault, &q1) != cudaSuccess || q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000, cudaEnableDefault,
+                                             &q2) != cudaSuccess || q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+    }
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 
 }  // namespace
 
@@ -190,16 +229,20 @@ int launch_knn_exact_noalloc(const float* base, int64_t n, const float* queries,
     float* D = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
+        NoAllocSlot& slot = g_noalloc_slot[dev];
+        const unsigned long long ctx = current_context_id();
+        if (!slot.ptr || ctx == 0 || ctx != slot.ctx) {
             void* p = nullptr;
             e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (e != cudaSuccess) return *why = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e), (int)e;
-            g_noalloc_ptr[dev] = static_cast<float*>(p);
+            slot.ptr = static_cast<float*>(p);
+            slot.ctx = current_context_id();                 // the lookup made the device's context current
         }
-        D = g_noalloc_ptr[dev];
+        D = slot.ptr;
     }
     // Every distance a chunk reads is written first by the same chunk: nothing needs clearing.
-    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(nq, kNoAllocScratchFloats / n));
+    // grid.y = ceil(chunk / kTile) stays within 65,535.
+    const int64_t chunk = std::max<int64_t>(1, std::min<int64_t>({nq, kNoAllocScratchFloats / n, kMaxChunkQueries}));
     for (int64_t q0 = 0; q0 < nq; q0 += chunk) {
         const int64_t qc = std::min(chunk, nq - q0);
         const dim3 grid((unsigned)((n + kTile - 1) / kTile), (unsigned)((qc + kTile - 1) / kTile));

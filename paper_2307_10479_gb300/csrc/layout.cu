@@ -5,9 +5,10 @@
 // pivot (float32 L2, ties -> lower pivot index), and vertices are ordered by (label, original
 // id) with a deterministic counting sort. Rows and the adjacency are then stored in that order.
 // A query's visited bitmap words, its rows and its adjacency rows then cluster in a few address
-// ranges, which keeps them in L2. Searches map caller ids in (seeds, exploration vertices) and
-// result ids out, so the layout is invisible to callers; the search keys order ties by internal
-// id.
+// ranges, which keeps them in L2. The adjacency stays indexed by caller id and holds, for every
+// neighbour, its internal id (to read its row and mark it visited) beside its caller id (the id in
+// the search keys, so distance ties are broken by caller id exactly as Alg. 1 over the caller's
+// numbering breaks them). The layout is invisible to callers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -150,13 +151,14 @@ __global__ void permute_rows_kernel(const float4* src, float4* dst, int64_t n, i
     }
 }
 
-__global__ void permute_adj_kernel(const int32_t* src, int32_t* dst, int64_t n, int32_t deg_pad, int32_t degree,
-                                   const int32_t* new2old, const int32_t* old2new) {
+// dst[v][j] = {internal id, caller id} of neighbour j of caller vertex v ({-1, -1} in padding).
+__global__ void pair_adj_kernel(const int32_t* src, int2* dst, int64_t n, int32_t deg_pad, int32_t degree,
+                                const int32_t* old2new) {
     const int64_t total = n * deg_pad;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t p = t / deg_pad;
-        const int j = (int)(t - p * deg_pad);
-        dst[t] = j < degree ? old2new[src[(int64_t)new2old[p] * deg_pad + j]] : -1;
+        const int j = (int)(t % deg_pad);
+        const int32_t v = j < degree ? src[t] : -1;
+        dst[t] = v >= 0 ? make_int2(old2new[v], v) : make_int2(-1, -1);
     }
 }
 
@@ -203,7 +205,7 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
         (e = cudaMalloc(&offsets, 4 * np)) != cudaSuccess || (e = cudaMalloc(&ix.old2new, 4 * n)) != cudaSuccess ||
         (e = cudaMalloc(&ix.new2old, 4 * n)) != cudaSuccess ||
         (e = cudaMalloc(&x2, sizeof(float) * n * ix.dim_pad)) != cudaSuccess ||
-        (e = cudaMalloc(&adj2, sizeof(int32_t) * n * ix.deg_pad)) != cudaSuccess ||
+        (e = cudaMalloc(&adj2, sizeof(int2) * n * ix.deg_pad)) != cudaSuccess ||
         (e = cudaMalloc(&d2, sizeof(float) * n)) != cudaSuccess) {
         cleanup();
         return *why = std::string("layout buffers: ") + cudaGetErrorString(e), (int)e;
@@ -217,7 +219,7 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
     scatter_ids_kernel<<<(unsigned)nchunks, 256, 0, st>>>(labels, n, np, chunk_hist, offsets, ix.old2new, ix.new2old);
     permute_rows_kernel<<<4096, 256, 0, st>>>(reinterpret_cast<const float4*>(ix.x32), reinterpret_cast<float4*>(x2), n,
                                               ix.dim_pad / 4, ix.new2old);
-    permute_adj_kernel<<<4096, 256, 0, st>>>(ix.adj, adj2, n, ix.deg_pad, ix.degree, ix.new2old, ix.old2new);
+    pair_adj_kernel<<<4096, 256, 0, st>>>(ix.adj, reinterpret_cast<int2*>(adj2), n, ix.deg_pad, ix.degree, ix.old2new);
     if ((e = cudaGetLastError()) == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         cleanup();

@@ -16,7 +16,9 @@
 //
 // Readings of Alg. 1 (as in the rest of the library): seeds count as checked; exploration
 // queries search from their own vertex but never return it; r = +inf until R first exceeds k;
-// (distance, id) orders S and R, the lower id first.
+// (distance, id) orders S and R, the lower id first. The id in a key is the caller's id, so ties
+// are broken exactly as Alg. 1 over the caller's numbering breaks them; the rows and the visited
+// bitmap use internal ids (the locality layout), which the adjacency carries beside each caller id.
 //
 // State of one query. The checked set C is an n-bit bitmap in the warp's slot of device memory
 // (cleared when the query starts). S is split in two: a "front" of at most F keys kept sorted
@@ -51,12 +53,38 @@ constexpr int kFront = 128;              // sorted on-chip part of S
 constexpr int kBackPool = 32768;         // device-memory part of S in the main kernel
 constexpr int kTouchCap = 8192;          // visited ids recorded per query for clearing C afterwards
 
+// Key of a candidate: squared distance bits (non-negative floats order as unsigned integers) over
+// the caller id of the vertex.
 __device__ __forceinline__ uint64_t make_key(float d2, int32_t id) {
     return ((uint64_t)__float_as_uint(d2) << 32) | (uint32_t)id;
 }
 __device__ __forceinline__ float key_d2(uint64_t k) { return __uint_as_float((uint32_t)(k >> 32)); }
 __device__ __forceinline__ int32_t key_id(uint64_t k) { return (int32_t)(uint32_t)k; }
 __device__ __forceinline__ unsigned lanes_below(int lane) { return (1u << lane) - 1u; }
+
+// (1 + eps)^2 as an unevaluated float sum hi + lo: Knuth's TwoSum for 1 + eps, then the square with
+// its rounding error recovered by an FMA (Dekker's product). The error term err^2 is below 2^-46
+// of hi and is dropped. Host code (the batch launch) and device code (the serving loop) run the
+// same float operations, so both get the same pair for the same eps.
+__host__ __device__ inline float2 eps_factor(float eps) {
+    const float s = 1.f + eps;
+    const float bb = s - 1.f;
+    const float err = (1.f - (s - bb)) + (eps - bb);          // 1 + eps = s + err exactly
+    const float p = s * s;
+    const float pe = fmaf(s, s, -p);                          // s^2 = p + pe exactly
+    return make_float2(p, fmaf(2.f * s, err, pe));
+}
+
+// The admission radius of Alg. 1, squared: d2 passes when d2 <= r2 (1 + eps)^2. The product is
+// compared through hi + lo, so the test is exact to about 2^-46 of r2 instead of float32's
+// rounding of r2 * (1 + eps)^2 (which differs from the real threshold by up to 2^-23 of it and
+// could flip the test for an integer-valued distance next to it). r2 = +inf before the first trim.
+struct Radius {
+    float r2, hi, lo;
+    __device__ __forceinline__ bool admits(float d2) const {
+        return r2 == __int_as_float(0x7f800000) || fmaf(-r2, hi, d2) <= r2 * lo;
+    }
+};
 
 __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
     const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
@@ -134,10 +162,11 @@ struct Params {
     const float2* norm8;       // FP8: per-row {scale s, s^2 ||x||^2}, or null
     const float* x32;          // float32 rows (exploration queries, re-rank)
     int32_t dim_pad;           // float32 row stride (elements)
-    const int32_t* adj;
+    const int2* adj;           // [n][deg_pad] {internal id, caller id} of each neighbour, row = caller id
     int32_t degree, deg_pad;
     int64_t n;
     int32_t entry;             // internal id
+    int32_t entry_caller;      // the same vertex's caller id
     const int32_t* old2new;    // caller id -> internal id
     const int32_t* new2old;    // internal id -> caller id
     const float* queries;
@@ -151,7 +180,7 @@ struct Params {
     int32_t ks;                // results kept during the search (k, or the re-rank width)
     int32_t kcap;              // power of two >= ks (sort width of a re-rank)
     int32_t rerank;            // 1: re-rank R on float32 rows before output
-    float f;                   // (1 + eps)^2
+    float f, f_lo;             // (1 + eps)^2 = f + f_lo (eps_factor)
     int32_t max_hops;
     int32_t wpb;               // warps per block
     // learned early stop (not in the paper): network weights, decision margin, trace recording
@@ -190,8 +219,9 @@ struct WarpState {
     uint64_t* front2;          // the other front buffer (a batched merge writes it, then they swap)
     uint64_t* back;            // S, the rest (device memory), [bcap]
     uint64_t* res;             // R, sorted ascending
-    int32_t* cid;              // per-hop candidate ids [kMaxDegree] (also the refill histogram)
+    int32_t* cid;              // per-hop candidate internal ids [kMaxDegree] (also the refill histogram)
     float* cd2;                // per-hop candidate distances [kMaxDegree]
+    int32_t* ccid;             // per-hop candidate caller ids [kMaxDegree]
     int32_t bcap;
     int32_t fn, back_n, res_n;
     uint64_t wmark;            // every front key < wmark <= every back key
@@ -394,14 +424,14 @@ __device__ float stop_margin(const __nv_bfloat16* w, const float* x, int lane) {
     return p + __bfloat162float(b3[1]) - __bfloat162float(b3[0]);
 }
 
-// Append to the back pool; on a full pool drop keys above thr first. False if still full.
-__device__ __forceinline__ bool back_push(WarpState& W, uint64_t c, float thr, int lane) {
+// Append to the back pool; on a full pool drop keys outside the radius first. False if still full.
+__device__ __forceinline__ bool back_push(WarpState& W, uint64_t c, const Radius& thr, int lane) {
     if (W.back_n == W.bcap) {
         int out = 0;
         for (int i0 = 0; i0 < W.back_n; i0 += 32) {
             const int i = i0 + lane;
             const uint64_t v = i < W.back_n ? W.back[i] : kEmptyKey;
-            const bool keep = i < W.back_n && key_d2(v) <= thr;
+            const bool keep = i < W.back_n && thr.admits(key_d2(v));
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             __syncwarp();
             if (keep) W.back[out + __popc(m & lanes_below(lane))] = v;
@@ -417,7 +447,7 @@ __device__ __forceinline__ bool back_push(WarpState& W, uint64_t c, float thr, i
 }
 
 // Add candidate c (admitted to S). False if the back pool overflowed.
-__device__ __forceinline__ bool s_insert(WarpState& W, uint64_t c, float thr, int lane) {
+__device__ __forceinline__ bool s_insert(WarpState& W, uint64_t c, const Radius& thr, int lane) {
     if (c >= W.wmark) return back_push(W, c, thr, lane);
     // position in the descending front: number of keys greater than c
     int pos = 0;
@@ -463,7 +493,7 @@ __device__ __forceinline__ bool s_insert(WarpState& W, uint64_t c, float thr, in
 // those. S ends as the same set as after one-by-one insertion, and every front key stays below
 // wmark <= every back key, so pops are unchanged. A batch that would overflow the back pool takes
 // the one-by-one path (which compacts the pool). False if the pool overflowed.
-__device__ bool admit_batch(WarpState& W, uint64_t key, bool take, float thr, int lane) {
+__device__ bool admit_batch(WarpState& W, uint64_t key, bool take, const Radius& thr, int lane) {
     const unsigned all = __ballot_sync(0xffffffffu, take);
     if (!all) return true;
     const bool toF = take && key < W.wmark;
@@ -578,13 +608,13 @@ __device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int 
 }
 
 // The front is empty: move the (up to) kFront smallest back keys into it, dropping back keys
-// above thr. Exact: the boundary is the (kFront+1)-th smallest key, found by radix select.
-__device__ void refill(WarpState& W, float thr, int lane) {
+// outside the radius. Exact: the boundary is the (kFront+1)-th smallest key, found by radix select.
+__device__ void refill(WarpState& W, const Radius& thr, int lane) {
     int out = 0;                                              // drop keys above the radius
     for (int i0 = 0; i0 < W.back_n; i0 += 32) {
         const int i = i0 + lane;
         const uint64_t v = i < W.back_n ? W.back[i] : kEmptyKey;
-        const bool keep = i < W.back_n && key_d2(v) <= thr;
+        const bool keep = i < W.back_n && thr.admits(key_d2(v));
         const unsigned m = __ballot_sync(0xffffffffu, keep);
         __syncwarp();
         if (keep) W.back[out + __popc(m & lanes_below(lane))] = v;
@@ -681,7 +711,7 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
     if (P.rerank) {
         for (int i = lane; i < W.res_n; i += 32) {
             const int32_t id = key_id(W.res[i]);
-            W.res[i] = make_key(exact_d2_lane(P.x32, P.dim_pad, id, qv), id);
+            W.res[i] = make_key(exact_d2_lane(P.x32, P.dim_pad, __ldg(P.old2new + id), qv), id);
         }
         for (int i = W.res_n + lane; i < P.kcap; i += 32) W.res[i] = kEmptyKey;
         __syncwarp();
@@ -699,7 +729,7 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
     for (int i = lane; i < P.k; i += 32) {
         const bool ok = i < W.res_n;
         const uint64_t v = ok ? W.res[i] : kEmptyKey;
-        P.ids[(int64_t)q * P.k + i] = ok ? __ldg(P.new2old + key_id(v)) : -1;
+        P.ids[(int64_t)q * P.k + i] = ok ? key_id(v) : -1;
         P.dists[(int64_t)q * P.k + i] = ok ? sqrtf(key_d2(v)) : __int_as_float(0x7f800000);
     }
     if (P.rec_feats) {
@@ -736,11 +766,13 @@ __device__ void clear_visited(WarpState& W, const Params& P, int lane) {
 
 template <class Rows, int G, int CPL>
 __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int tier, int lane) {
-    // seeds and exploration vertices come in caller ids; the search runs on internal ids
+    // seeds and exploration vertices come in caller ids (routed seeds in internal ids); rows are
+    // read by internal id, keys carry the caller id
     const bool given = P.explore || P.seeds;
     const int32_t seed_in = given ? P.seeds[q] : 0;
     const bool seed_ok = !given || (seed_in >= 0 && seed_in < P.n);
     const int32_t seed = !given ? P.entry : (!seed_ok ? 0 : P.seeds_internal ? seed_in : __ldg(P.old2new + seed_in));
+    const int32_t seed_c = !given ? P.entry_caller : (!seed_ok ? 0 : P.seeds_internal ? __ldg(P.new2old + seed_in) : seed_in);
     const float* qsrc = P.explore ? P.x32 + (int64_t)(seed_ok ? seed : 0) * P.dim_pad : P.queries + (int64_t)q * P.dim;
     const int dim4 = (P.dim + 3) / 4 * 4;
     for (int i = lane; i < dim4; i += 32) qv_smem[i] = i < P.dim ? qsrc[i] : 0.f;
@@ -776,7 +808,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     eng.distances(P, W.cid, W.cd2, 1, lane);
     if (lane == 0) visit(W.bitmap, seed);
     __syncwarp();
-    const uint64_t seed_key = make_key(W.cd2[0], seed);
+    const uint64_t seed_key = make_key(W.cd2[0], seed_c);
     if (lane == 0) W.front[0] = seed_key;
     W.fn = 1;
     W.peak = 1;
@@ -787,7 +819,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     const float inf = __int_as_float(0x7f800000);
     int status = DEG_OK;
     for (;;) {
-        const float thr = W.trimmed ? W.r2 * P.f : inf;
+        const Radius thr{W.trimmed ? W.r2 : inf, P.f, P.f_lo};
         if (W.fn == 0) {
             if (W.back_n == 0) break;                          // S empty
             refill(W, thr, lane);
@@ -795,18 +827,19 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         // 1. pop the minimum of S (the front's last key)
         const uint64_t m = W.front[W.fn - 1];
-        if (key_d2(m) > thr) break;                            // too far: return R
+        if (!thr.admits(key_d2(m))) break;                     // too far: return R
         if (P.max_hops && W.hops >= P.max_hops) { status = DEG_EHOPLIMIT; break; }
         --W.fn;
         ++W.hops;
-        const int32_t s = key_id(m);
+        const int32_t s = key_id(m);                           // caller id: the adjacency row
         __syncwarp();
 
         // 2. N(G, s) \ C, then C <- C u N
         int cnt = 0;
         for (int j0 = 0; j0 < P.degree; j0 += 32) {
             const int j = j0 + lane;
-            const int32_t nb = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : -1;
+            const int2 e = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : make_int2(-1, -1);
+            const int32_t nb = e.x;
             if (nb >= 0 && P.row_bytes <= 256) {
                 // start pulling the row into L2 while the visited test is in flight (a visited
                 // neighbour's row is usually there already); float32 rows (four lines) lose by it
@@ -816,7 +849,11 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             }
             const int isnew = nb >= 0 ? visit(W.bitmap, nb) : 0;
             const unsigned nm = __ballot_sync(0xffffffffu, isnew);
-            if (isnew) W.cid[cnt + __popc(nm & lanes_below(lane))] = nb;
+            if (isnew) {
+                const int at = cnt + __popc(nm & lanes_below(lane));
+                W.cid[at] = nb;
+                W.ccid[at] = e.y;
+            }
             cnt += __popc(nm);
         }
         __syncwarp();
@@ -832,16 +869,16 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
 
         // 4. admit against the radius from before the hop
         const float r2pre = W.trimmed ? W.r2 : inf;
-        const float thrpre = W.trimmed ? W.r2 * P.f : inf;
+        const Radius thrpre{r2pre, P.f, P.f_lo};
         int adm = 0;
         W.hop_rins = 0;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < cnt;
             const float d2 = valid ? W.cd2[i] : inf;
-            const int32_t id = valid ? W.cid[i] : -1;
+            const int32_t id = valid ? W.ccid[i] : -1;
             const uint64_t key = make_key(d2, id);
-            const bool toS = valid && d2 <= thrpre;
+            const bool toS = valid && thrpre.admits(d2);
             if (toS)  // its adjacency row is read if it is ever expanded: start pulling it into L2
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
             adm += __popc(__ballot_sync(0xffffffffu, toS));
@@ -870,7 +907,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
 
 // Shared-memory bytes per warp.
 __host__ __device__ inline int64_t warp_bytes(int kcap, int dim) {
-    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 3) / 4 * 4);
+    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 3) / 4 * 4);
     return (b + 15) / 16 * 16;
 }
 
@@ -880,7 +917,8 @@ __device__ __forceinline__ float* bind_smem(WarpState& W, uint8_t* base, const P
     W.res = W.front2 + kFront;
     W.cid = reinterpret_cast<int32_t*>(W.res + P.kcap);
     W.cd2 = reinterpret_cast<float*>(W.cid + kMaxDegree);
-    W.fbuf = reinterpret_cast<uint64_t*>(W.cd2 + kMaxDegree);
+    W.ccid = reinterpret_cast<int32_t*>(W.cd2 + kMaxDegree);
+    W.fbuf = reinterpret_cast<uint64_t*>(W.ccid + kMaxDegree);
     return reinterpret_cast<float*>(W.fbuf + 32);
 }
 
@@ -1039,7 +1077,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
         Params Q = P;
         Q.k = m.x;
         Q.ks = P.rerank ? max(P.ks, m.x) : m.x;
-        Q.f = (1.f + __int_as_float(m.y)) * (1.f + __int_as_float(m.y));
+        const float2 fe = eps_factor(__int_as_float(m.y));
+        Q.f = fe.x;
+        Q.f_lo = fe.y;
         Q.nq = 1;
         Q.ids = S.ids + (int64_t)r * S.kmax;
         Q.dists = S.dists + (int64_t)r * S.kmax;
@@ -1237,11 +1277,12 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     Params P{};
     P.x32 = ix.x32;
     P.dim_pad = ix.dim_pad;
-    P.adj = ix.adj;
+    P.adj = reinterpret_cast<const int2*>(ix.adj);
     P.degree = ix.degree;
     P.deg_pad = ix.deg_pad;
     P.n = ix.n;
     P.entry = ix.entry_internal;
+    P.entry_caller = ix.entry;
     P.old2new = ix.old2new;
     P.new2old = ix.new2old;
     P.queries = a.queries;
@@ -1264,7 +1305,9 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.ks = reduced && a.rerank ? std::max(a.rerank, a.k) : a.k;
     P.kcap = std::max(32, pow2_at_least(P.ks));
     P.rerank = reduced ? 1 : 0;
-    P.f = (float)((1.0 + (double)a.eps) * (1.0 + (double)a.eps));
+    const float2 fe = eps_factor(a.eps);
+    P.f = fe.x;
+    P.f_lo = fe.y;
     P.max_hops = a.max_hops;
     P.learned = a.learned_stop ? 1 : 0;
     P.stop_w = reinterpret_cast<const __nv_bfloat16*>(ix.stop_w);
@@ -1322,11 +1365,12 @@ int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* 
     Params P{};
     P.x32 = ix.x32;
     P.dim_pad = ix.dim_pad;
-    P.adj = ix.adj;
+    P.adj = reinterpret_cast<const int2*>(ix.adj);
     P.degree = ix.degree;
     P.deg_pad = ix.deg_pad;
     P.n = ix.n;
     P.entry = ix.entry_internal;
+    P.entry_caller = ix.entry;
     P.old2new = ix.old2new;
     P.new2old = ix.new2old;
     P.dim = ix.dim;

@@ -8,6 +8,11 @@ import numpy as np
 REL = 1e-5
 
 
+def eps32(eps):
+    """The eps a search of the library ran with: the C ABI takes eps as a float32."""
+    return float(np.float32(eps))
+
+
 def recall(ids, gt):
     k = ids.shape[1]
     return float(np.mean([len(set(a.tolist()) & set(b.tolist())) / k for a, b in zip(ids, gt[:, :k])]))

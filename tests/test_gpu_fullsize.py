@@ -3,10 +3,10 @@ configuration (all 10,000 queries in one launch), checked on 200 sampled queries
 oracle searches one by one from the same graph file.
 
 The rows are integers (the mixture's coordinates are rounded to 0..255), so float32 squared
-distances are exact (at most 128 * 255^2 < 2^24) and the plain float32 form must match the
-oracle's results, hops and evaluations. Exact ties are the exception: the GPU breaks them by its
-internal row order after the locality layout, the oracle by caller id. compare_lists accepts such
-a swap of equal-distance ids and counts the query as not identical. The FP8 form computes in
+distances are exact (at most 128 * 255^2 < 2^24). Both sides break exact distance ties by the
+caller's id, and the kernel's admission test r^2 (1 + eps)^2 is exact to about 2^-46, so the plain
+float32 form must match the oracle's results, hops and evaluations on every sampled query (the
+oracle gets the float32 eps the library searched with). The FP8 form computes in
 float32 on decoded codes (rounding differs from the oracle's FP64), so it is held to identical
 lists on most sampled queries, the same recall, and re-ranked distances equal to the float32
 rows'."""
@@ -18,7 +18,7 @@ import pytest
 import bench
 import oracle
 from paper_2307_10479_gb300 import graphs, synth
-from parity import compare_lists, recall
+from parity import compare_lists, eps32, recall
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -53,14 +53,14 @@ def test_plain_float32_form_matches_the_oracle_exactly(full):
     torch.cuda.synchronize()
     ids, d, st, tr = ids.cpu().numpy(), d.cpu().numpy(), st.cpu().numpy(), tr.cpu().numpy()
     assert (st == 0).all()
-    o_ids, o_d, o_tr = oracle.range_search(base, adj, qs, np.full(len(qs), full["entry"], np.int32), 10, eps)
-    # every differing query may differ only by a swap of equal distances (compare_lists asserts it);
-    # 1% of these sampled queries have an exact tie between their 10th and 11th neighbour
-    frac, diff = compare_lists(ids[SAMPLE], d[SAMPLE], o_ids, o_d, min_identical=0.95)
+    o_ids, o_d, o_tr = oracle.range_search(base, adj, qs, np.full(len(qs), full["entry"], np.int32), 10, eps32(eps))
+    # 1% of these sampled queries have an exact tie between their 10th and 11th neighbour: both
+    # sides keep the lower caller id
+    frac, diff = compare_lists(ids[SAMPLE], d[SAMPLE], o_ids, o_d, min_identical=0.999)
     same = np.ones(len(qs), bool)
     same[diff] = False
-    assert np.mean(tr[SAMPLE][same, 0] == o_tr[same, 0]) >= 0.97      # hops H
-    assert np.mean(tr[SAMPLE][same, 1] == o_tr[same, 1]) >= 0.97      # evaluations E
+    assert np.mean(tr[SAMPLE][same, 0] == o_tr[same, 0]) >= 0.999     # hops H
+    assert np.mean(tr[SAMPLE][same, 1] == o_tr[same, 1]) >= 0.999     # evaluations E
 
 
 def test_headline_fp8_form_against_the_oracle(full):
@@ -78,7 +78,7 @@ def test_headline_fp8_form_against_the_oracle(full):
     lab, _ = oracle.knn_bruteforce(base[piv], qs, 1)
     codes, scales = oracle.quantize_fp8(base)
     dec = oracle.decode("fp8", codes, scales)
-    o_ids, o_d = oracle.range_search_decoded(dec, base, adj, qs, piv[lab[:, 0]], 10, eps, keep=32)
+    o_ids, o_d = oracle.range_search_decoded(dec, base, adj, qs, piv[lab[:, 0]], 10, eps32(eps), keep=32)
     del dec
     same = np.all(ids == o_ids, axis=1)
     assert same.mean() >= 0.95, f"{same.mean():.3f} of the sampled lists identical"

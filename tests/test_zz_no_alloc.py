@@ -44,6 +44,24 @@ def test_noalloc_knn_matches_knn_exact_on_consecutive_calls():
     assert st == deg.DEG_OK and torch.equal(ids, r_ids)
 
 
+@pytest.mark.parametrize("n,nq", [(8 << 20, 3), (2, 65535 * 64 + 70)])
+def test_noalloc_at_the_chunking_extremes(n, nq):
+    # n = 8,388,608 rows fills the scratch with one query per chunk; n = 2 rows with more than
+    # 65,535 * 64 queries needs a second chunk because one launch takes at most 65,535 * 64 queries
+    import paper_2307_10479_gb300 as deg
+    lib = deg.lib()
+    g = torch.Generator(device="cuda").manual_seed(5)
+    base = torch.rand((n, 4), generator=g, device="cuda")
+    q = torch.rand((nq, 4), generator=g, device="cuda")
+    ref_ids, ref_d = deg.knn_exact(base, q, 1)
+    for _ in range(2):
+        st, ids, d = _noalloc(lib, base, q, 1)
+        assert st == deg.DEG_OK, lib.deg_last_error()
+        torch.cuda.synchronize()
+        assert torch.equal(ids, ref_ids)
+        assert torch.allclose(d, ref_d, rtol=1e-5, atol=0)
+
+
 def test_noalloc_rejects_a_base_larger_than_its_scratch():
     import paper_2307_10479_gb300 as deg
     lib = deg.lib()

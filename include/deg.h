@@ -81,6 +81,27 @@ typedef struct deg_index deg_index;   /* opaque, owned by the library */
 DEG_API deg_status deg_build(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
                      volatile int64_t* progress, deg_index** out);
 
+/* Build a DEG over base_host [n][dim] float32 on the current GPU: ExtendGraph (Sec. 5.2, Alg. 3,
+ * scheme C with the checkMRNG test of Alg. 2 in a first pass) for batches of new vertices at a
+ * time. Each batch is searched over the graph built so far by the library's search kernels
+ * (Alg. 1: seed vertex 0, k_ext results, eps_ext); one warp per new vertex then replaces edges
+ * (b, n) by (v, b), (v, n). A batch holds at most 1/batch_div of the vertices already inserted
+ * (at least 1, at most 8,192), so the vertices of a batch rarely fall in each other's
+ * neighbourhoods; old vertices are claimed per batch, so two new vertices never rewire the same
+ * vertex in one batch, and a vertex that runs out of free candidates is inserted again later with
+ * more candidates. The optional optimizeEdge step of Alg. 3 (k_opt, eps_opt, i_opt) and
+ * refine_rounds are not applied: the result is the paper's construction-only graph (App. G). The
+ * graph is an even-regular, symmetric, connected graph without loops or duplicates (checked
+ * before returning; DEG_EGRAPH otherwise), but not the graph the sequential builder makes: which
+ * new vertex claims an old vertex first depends on the order the warps run in. Copies the vectors;
+ * device memory about n * (4 dim + 12 degree) bytes plus the search scratch, all freed before
+ * returning. Synchronises `stream`. DEG_EINVAL when dim is outside 1 ... 1024, degree is odd or
+ * outside 4 ... 128, n < degree + 1 or above 2^31 - 1, k_ext is outside degree ... 1024, eps_ext
+ * < 0 or batch_div < 1; DEG_ECUDA on a device error. progress (nullable) receives the number of
+ * vertices inserted so far. */
+DEG_API deg_status deg_build_device(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
+                                    int32_t batch_div, volatile int64_t* progress, deg_index** out, void* stream);
+
 /* Wrap an existing graph: base_host [n][dim] float32 and adj_host [n][degree] int32 are copied.
  * The adjacency is checked (every entry in [0,n), no self-loops, no duplicates, symmetric,
  * degree even and >= 4): DEG_EGRAPH if it is not a valid undirected regular graph. */
@@ -147,6 +168,13 @@ typedef struct {
 DEG_API deg_status deg_search(deg_index* idx, const float* queries_dev, int64_t nq, int32_t k, float eps,
                       const int32_t* seeds_dev, int32_t* ids_dev, float* dists_dev,
                       int32_t* status_dev, void* stream);
+
+/* Instrumentation, not in the paper: every later search call on idx records start_event on its
+ * stream just before the main search kernel (after any entry routing) and end_event just after
+ * the second kernel, so cudaEventElapsedTime gives the search kernels' own time. The events are
+ * cudaEvent_t handles the caller creates and owns; NULL, NULL stops the recording. DEG_EINVAL if
+ * only one is NULL. Not thread-safe against concurrent searches on the same index. */
+DEG_API deg_status deg_set_kernel_timer(deg_index* idx, void* start_event, void* end_event);
 
 /* Exploration (Sec. 6.7): query q is the indexed vertex vertex_ids_dev[q]; the search starts
  * at that vertex and never returns it (the user has already seen it). */
@@ -262,8 +290,11 @@ DEG_API deg_status deg_serve_stop(deg_server* srv);
 /* ---- exact ground truth (Eq. 1) ----------------------------------------------------------- */
 
 /* Exact k nearest neighbours of queries_dev [nq][dim] among base_dev [n][dim] (float32 rows,
- * row-major, dim floats apart), 1 <= k <= 256. Distances are the float32 Euclidean distances
- * the library's search uses; ties go to the lower id. */
+ * row-major, dim floats apart), 1 <= k <= 1024. Distances are the float32 Euclidean distances
+ * the library's search uses; ties go to the lower id. Up to k = 256 the distances come from
+ * bfloat16 tensor-core products and every row within a proven rounding bound is re-scored in
+ * float32; above 256 every distance is computed in float32 on the CUDA cores. Both give the same
+ * result. Allocates its scratch and synchronises the stream. */
 DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
                      int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
 

@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         S = ctypes.c_int
         sig = {
             "deg_build": (S, [P, i64, i32, ctypes.POINTER(BuildParams), P, ctypes.POINTER(P)]),
+            "deg_build_device": (S, [P, i64, i32, ctypes.POINTER(BuildParams), i32, P, ctypes.POINTER(P), P]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -78,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "deg_search": (S, [P, P, i64, i32, f32, P, P, P, P, P]),
             "deg_explore": (S, [P, P, i64, i32, f32, P, P, P, P]),
             "deg_search_ex": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P, P, P]),
+            "deg_set_kernel_timer": (S, [P, P, P]),
             "deg_search_host": (S, [P, ctypes.POINTER(SearchParams), P, P, i32, i64, P, P, P]),
             "knn_exact": (S, [P, i64, P, i64, i32, i32, P, P, P]),
             "knn_exact_noalloc": (S, [P, i64, P, i64, i32, i32, P, P, P]),
@@ -148,6 +150,17 @@ class Index:
         p = BuildParams(degree, k_ext, eps_ext, k_opt, eps_opt, i_opt, refine_rounds, seed)
         h = ctypes.c_void_p()
         _check(lib().deg_build(base.ctypes.data, base.shape[0], base.shape[1], ctypes.byref(p), None, ctypes.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def build_device(cls, base: np.ndarray, degree: int, k_ext: int, eps_ext: float, batch_div: int = 256,
+                     stream=None) -> "Index":
+        """ExtendGraph in batches on the current GPU (deg_build_device); no edge optimisation."""
+        base = np.ascontiguousarray(base, np.float32)
+        p = BuildParams(degree, k_ext, eps_ext, degree, 0.001, 0, 0, 0)
+        h = ctypes.c_void_p()
+        _check(lib().deg_build_device(base.ctypes.data, base.shape[0], base.shape[1], ctypes.byref(p), batch_div, None,
+                                      ctypes.byref(h), _stream_ptr(stream)))
         return cls(h)
 
     @classmethod
@@ -236,6 +249,11 @@ class Index:
         if with_trace:
             res.append(trace)
         return tuple(res)
+
+    def set_kernel_timer(self, start=None, end=None):
+        """Record torch.cuda.Event start/end around the search kernels of later calls (None: stop)."""
+        _check(lib().deg_set_kernel_timer(self._h, None if start is None else ctypes.c_void_p(start.cuda_event),
+                                          None if end is None else ctypes.c_void_p(end.cuda_event)))
 
     def search_host(self, queries: np.ndarray | None, k: int, eps: float, explore_ids: np.ndarray | None = None,
                     precision: str = "f32", rerank: int = 0, entry: str = "fixed", learned_stop: bool = False,

@@ -25,6 +25,8 @@ struct deg_index {
     deg::Workspace ws;
     int device = -1;
     int32_t uploaded_mask = 0;
+    void* timer_start = nullptr;  // cudaEvent_t pair recorded around the search kernels (or null)
+    void* timer_end = nullptr;
 };
 
 namespace deg {
@@ -150,6 +152,38 @@ extern "C" deg_status deg_build(const float* base_host, int64_t n, int32_t dim, 
     } catch (const std::exception& e) {
         delete idx;
         return fail(DEG_EGRAPH, std::string("deg_build: ") + e.what());
+    }
+    *out = idx;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_build_device(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
+                                       int32_t batch_div, volatile int64_t* progress, deg_index** out, void* stream) {
+    if (!out) return fail(DEG_EINVAL, "deg_build_device: out is NULL");
+    *out = nullptr;
+    if (!base_host || !p) return fail(DEG_EINVAL, "deg_build_device: NULL argument");
+    if (dim <= 0 || dim > 1024) return fail(DEG_EINVAL, "deg_build_device: dim must be in [1, 1024]");
+    if (p->degree < 4 || p->degree % 2 || p->degree > 128)
+        return fail(DEG_EINVAL, "deg_build_device: degree must be even and in [4, 128]");
+    if (n < p->degree + 1) return fail(DEG_EINVAL, "deg_build_device: need n >= degree + 1");
+    if (n > INT32_MAX) return fail(DEG_EINVAL, "deg_build_device: n must fit in int32");
+    if (p->k_ext < p->degree || p->k_ext > 1024) return fail(DEG_EINVAL, "deg_build_device: need degree <= k_ext <= 1024");
+    if (!(p->eps_ext >= 0.f)) return fail(DEG_EINVAL, "deg_build_device: eps_ext must be >= 0");
+    if (batch_div < 1) return fail(DEG_EINVAL, "deg_build_device: batch_div must be >= 1");
+    deg_index* idx = new_index(n, dim, p->degree);
+    if (!idx) return fail(DEG_ENOMEM, "deg_build_device: host allocation failed");
+    std::memcpy(idx->x.data(), base_host, sizeof(float) * (size_t)n * dim);
+    std::string why;
+    const int e = build_graph_device(idx->x.data(), n, dim, *p, batch_div, idx->adj.data(), progress,
+                                     static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) {
+        delete idx;
+        return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "deg_build_device: " + why);
+    }
+    const deg_status s = check_graph(idx->adj.data(), n, p->degree);
+    if (s != DEG_OK) {
+        delete idx;
+        return s;
     }
     *out = idx;
     return DEG_OK;
@@ -387,8 +421,19 @@ extern "C" deg_status deg_search_ex(deg_index* idx, const deg_search_params* p, 
     SearchArgs a{&idx->dev, queries_dev, seeds_dev, explore ? 1 : 0, nq, p->k, p->eps, p->precision,
                  p->rerank, p->max_hops, p->visited_cap, p->queue_cap, p->entry_mode, p->learned_stop ? 1 : 0,
                  nullptr, nullptr, nullptr, 0, ids_dev, dists_dev, status_dev, trace_dev};
+    a.timer_start = idx->timer_start;
+    a.timer_end = idx->timer_end;
     const int e = launch_search(a, idx->ws, static_cast<deg_stream_t>(stream), &why);
     if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "search: " + why);
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_set_kernel_timer(deg_index* idx, void* start_event, void* end_event) {
+    if (!idx) return fail(DEG_EINVAL, "set_kernel_timer: NULL index");
+    if ((start_event == nullptr) != (end_event == nullptr))
+        return fail(DEG_EINVAL, "set_kernel_timer: give both events or neither");
+    idx->timer_start = start_event;
+    idx->timer_end = end_event;
     return DEG_OK;
 }
 
@@ -450,13 +495,17 @@ extern "C" deg_status deg_search_host(deg_index* idx, const deg_search_params* p
 extern "C" deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
                                 int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream) {
     if (n <= 0 || n > INT32_MAX || nq < 0 || nq > INT32_MAX || dim <= 0) return fail(DEG_EINVAL, "knn_exact: bad sizes");
-    if (k < 1 || k > 256) return fail(DEG_EINVAL, "knn_exact: k must be in [1, 256]");
+    if (k < 1 || k > 1024) return fail(DEG_EINVAL, "knn_exact: k must be in [1, 1024]");
     if (k > n) return fail(DEG_EINVAL, "knn_exact: k larger than n");
     if (nq == 0) return DEG_OK;
     if (!base_dev || !queries_dev || !ids_dev || !dists_dev) return fail(DEG_EINVAL, "knn_exact: NULL argument");
     std::string why;
-    const int e = launch_knn_exact(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
-                                   static_cast<deg_stream_t>(stream), &why);
+    // k above 256 (ground truth for long lists): the CUDA-core path, whose result the tensor-core
+    // path reproduces bit for bit at k <= 256
+    const int e = k <= 256 ? launch_knn_exact(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
+                                              static_cast<deg_stream_t>(stream), &why)
+                           : launch_knn_simt(base_dev, n, queries_dev, nq, dim, k, ids_dev, dists_dev,
+                                             static_cast<deg_stream_t>(stream), &why);
     if (e != 0) return fail(DEG_ECUDA, "knn_exact: " + why);
     return DEG_OK;
 }
@@ -465,7 +514,7 @@ extern "C" deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const 
                                         int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream) {
     if (n <= 0 || n > INT32_MAX || nq < 0 || nq > INT32_MAX || dim <= 0)
         return fail(DEG_EINVAL, "knn_exact_noalloc: bad sizes");
-    if (k < 1 || k > 256) return fail(DEG_EINVAL, "knn_exact_noalloc: k must be in [1, 256]");
+    if (k < 1 || k > 1024) return fail(DEG_EINVAL, "knn_exact_noalloc: k must be in [1, 1024]");
     if (k > n) return fail(DEG_EINVAL, "knn_exact_noalloc: k larger than n");
     if (n > (8ll << 20)) return fail(DEG_EINVAL, "knn_exact_noalloc: n exceeds the static scratch (at most 8388608 base rows)");
     if (nq == 0) return DEG_OK;

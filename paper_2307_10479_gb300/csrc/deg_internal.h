@@ -20,6 +20,11 @@ constexpr int kStopParams = 5122;   // 12*64 + 64 + 64*64 + 64 + 2*64 + 2
 int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& p, int32_t* adj_out,
                 volatile int64_t* progress);
 
+// Device construction (build_gpu.cu): batched ExtendGraph on the current device, adjacency
+// [n][degree] written to adj_out (host). Returns a cudaError_t value (0 = success).
+int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,
+                       int32_t* adj_out, volatile int64_t* progress, deg_stream_t stream, std::string* why);
+
 // Record an error message for deg_last_error() and return the status.
 deg_status fail(deg_status s, const std::string& msg);
 
@@ -99,6 +104,9 @@ struct SearchArgs {
     float* dists;
     int32_t* status;
     int32_t* trace;
+    const int32_t* seeds2 = nullptr;   // [nq] second seed per query (caller id, -1 = none), or null
+    void* timer_start = nullptr;   // cudaEvent_t recorded just before the main search kernel
+    void* timer_end = nullptr;     // cudaEvent_t recorded just after the second kernel
 };
 
 // Serving ring (device pointers into mapped host memory, plus two device words).

@@ -69,7 +69,7 @@ constexpr int kSelThreads = 1024;
 __global__ void __launch_bounds__(kSelThreads) select_topk_kernel(const float* __restrict__ D, int64_t n, int k,
                                                                  int32_t* ids, float* dists) {
     __shared__ uint32_t hist[256];
-    __shared__ unsigned long long keys[512];
+    __shared__ unsigned long long keys[1024];              // k <= 1024
     __shared__ uint64_t prefix_s;
     __shared__ uint32_t rank_s;
     __shared__ int count_s;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(kSelThreads) select_topk_kernel(const float* _
         const uint64_t key = ((uint64_t)__float_as_uint(d[i]) << 32) | (uint32_t)i;
         if (key <= kth) {
             const int p = atomicAdd(&count_s, 1);
-            if (p < 512) keys[p] = key;
+            if (p < 1024) keys[p] = key;
         }
     }
     __syncthreads();

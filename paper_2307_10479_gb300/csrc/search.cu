@@ -172,6 +172,7 @@ struct Params {
     const float* queries;
     int32_t dim;
     const int32_t* seeds;
+    const int32_t* seeds2;     // a second seed per query (caller id, -1 = none), or null
     int32_t seeds_internal;    // 1: seeds are internal ids already (pivot routing)
     const int32_t* order;      // work order of the main kernel (queries far from their pivot first), or null
     int32_t explore;
@@ -815,6 +816,34 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     W.evals = 1;
     if (!P.explore) result_insert(W, P.ks, seed_key, lane);
     __syncwarp();
+    if (P.seeds2) {
+        // a second seed (Alg. 1 takes a seed set; the device builder's optimizeEdge searches from
+        // two vertices): S, C and R get it too, unless it is absent (-1), out of range or the first
+        const int32_t s2c = P.seeds2[q];
+        if (s2c >= 0 && s2c < P.n && s2c != seed_c) {
+            const int32_t s2 = __ldg(P.old2new + s2c);
+            if (lane == 0) {
+                W.cid[0] = s2;
+                if (W.touched) W.touched[1] = s2;
+            }
+            __syncwarp();
+            eng.distances(P, W.cid, W.cd2, 1, lane);
+            if (lane == 0) visit(W.bitmap, s2);
+            __syncwarp();
+            const uint64_t k2 = make_key(W.cd2[0], s2c);
+            if (lane == 0) {                                  // the front stays sorted descending
+                if (k2 < W.front[0]) W.front[1] = k2;
+                else { W.front[1] = W.front[0]; W.front[0] = k2; }
+            }
+            W.fn = 2;
+            W.peak = 2;
+            W.evals = 2;
+            W.tn = 2;
+            __syncwarp();
+            if (!P.explore) result_insert(W, P.ks, k2, lane);
+            __syncwarp();
+        }
+    }
 
     const float inf = __int_as_float(0x7f800000);
     int status = DEG_OK;
@@ -1154,7 +1183,7 @@ int dispatch_serve(Params P, const ServeRing& S, const int32_t* pivots, int np, 
 }
 
 template <class Rows, int G, int CPL>
-int launch_typed(Params P, cudaStream_t st, std::string* why) {
+int launch_typed(Params P, cudaStream_t st, void* timer_start, void* timer_end, std::string* why) {
     cudaError_t e;
     int dev = 0, smem_max = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -1175,6 +1204,8 @@ int launch_typed(Params P, cudaStream_t st, std::string* why) {
     const int64_t want = (P.nq + wpb - 1) / wpb;
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>({want, (int64_t)sms * per_sm, (int64_t)P.slots / wpb}));
     if ((e = cudaMemsetAsync(P.counters, 0, 4 * sizeof(int32_t), st)) != cudaSuccess) return *why = "memset", (int)e;
+    if (timer_start && (e = cudaEventRecord(static_cast<cudaEvent_t>(timer_start), st)) != cudaSuccess)
+        return *why = "timer event", (int)e;
     fk<<<(unsigned)grid, wpb * 32, smem, st>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return *why = std::string("main kernel: ") + cudaGetErrorString(e), (int)e;
     auto dk = search_device_kernel<Rows, G, CPL>;
@@ -1184,19 +1215,21 @@ int launch_typed(Params P, cudaStream_t st, std::string* why) {
         return *why = "second kernel attribute", (int)e;
     dk<<<(P.pslots + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, dsm, st>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return *why = std::string("second kernel: ") + cudaGetErrorString(e), (int)e;
+    if (timer_end && (e = cudaEventRecord(static_cast<cudaEvent_t>(timer_end), st)) != cudaSuccess)
+        return *why = "timer event", (int)e;
     return 0;
 }
 
 template <class Rows>
-int dispatch_shape(Params P, cudaStream_t st, std::string* why) {
+int dispatch_shape(Params P, cudaStream_t st, void* t0, void* t1, std::string* why) {
     const int nc = P.nchunk;
-    if (nc <= 4) return launch_typed<Rows, 4, 1>(P, st, why);
-    if (nc <= 8) return launch_typed<Rows, 8, 1>(P, st, why);
-    if (nc <= 16) return launch_typed<Rows, 16, 1>(P, st, why);
-    if (nc <= 32) return launch_typed<Rows, 32, 1>(P, st, why);
-    if (nc <= 64) return launch_typed<Rows, 32, 2>(P, st, why);
-    if (nc <= 128) return launch_typed<Rows, 32, 4>(P, st, why);
-    if (nc <= 256) return launch_typed<Rows, 32, 8>(P, st, why);
+    if (nc <= 4) return launch_typed<Rows, 4, 1>(P, st, t0, t1, why);
+    if (nc <= 8) return launch_typed<Rows, 8, 1>(P, st, t0, t1, why);
+    if (nc <= 16) return launch_typed<Rows, 16, 1>(P, st, t0, t1, why);
+    if (nc <= 32) return launch_typed<Rows, 32, 1>(P, st, t0, t1, why);
+    if (nc <= 64) return launch_typed<Rows, 32, 2>(P, st, t0, t1, why);
+    if (nc <= 128) return launch_typed<Rows, 32, 4>(P, st, t0, t1, why);
+    if (nc <= 256) return launch_typed<Rows, 32, 8>(P, st, t0, t1, why);
     *why = "row too wide (at most 4096 bytes)";
     return (int)cudaErrorInvalidValue;
 }
@@ -1288,6 +1321,7 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.queries = a.queries;
     P.dim = ix.dim;
     P.seeds = a.seeds;
+    P.seeds2 = a.seeds2;
     P.explore = a.explore;
     if (a.entry_mode == 1 && !a.explore && !a.seeds) {
         // route every query to its nearest pivot first; those become internal seeds
@@ -1339,19 +1373,19 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
         P.rows = reinterpret_cast<const uint8_t*>(ix.x32);
         P.row_bytes = 4ll * ix.dim_pad;
         P.nchunk = ix.dim_pad / 4;
-        return dispatch_shape<F32Rows>(P, st, why);
+        return dispatch_shape<F32Rows>(P, st, a.timer_start, a.timer_end, why);
     }
     if (a.precision == DEG_BF16) {
         P.rows = reinterpret_cast<const uint8_t*>(ix.xbf);
         P.row_bytes = 2ll * ix.dim_pad16;
         P.nchunk = ix.dim_pad16 / 8;
-        return dispatch_shape<BF16Rows>(P, st, why);
+        return dispatch_shape<BF16Rows>(P, st, a.timer_start, a.timer_end, why);
     }
     P.rows = ix.x8;
     P.row_bytes = ix.dim_pad8;
     P.nchunk = ix.dim_pad8 / 16;
     P.norm8 = reinterpret_cast<const float2*>(ix.norm8);
-    return dispatch_shape<FP8Rows>(P, st, why);
+    return dispatch_shape<FP8Rows>(P, st, a.timer_start, a.timer_end, why);
 }
 
 }  // namespace deg

@@ -154,3 +154,17 @@ def test_nearest_rows_overflow_scores_every_row():
         deg.nearest_rows(r, qq, cap=3)
     with pytest.raises(deg.DegError):
         deg.nearest_rows(torch.zeros((4097, 16), device="cuda"), qq)
+
+
+def test_knn_exact_up_to_k_1024_integer_data_is_bit_exact():
+    # k above 256 (the ground truth of k = 1,000 exploration) on integer rows: exact, ties by id
+    import paper_2307_10479_gb300 as deg
+    w = synth.scaled(synth.WORKLOADS["sift-1m-d128"], 20_000, 40)
+    base, q = w.base(), w.queries()
+    for k in (257, 1000, 1024):
+        ids, d = deg.knn_exact(torch.from_numpy(base).cuda(), torch.from_numpy(q).cuda(), k)
+        o_ids, o_d = oracle.knn_bruteforce(base, q, k)
+        assert np.array_equal(ids.cpu().numpy(), o_ids)
+        assert np.array_equal(d.cpu().numpy().astype(np.float64), o_d.astype(np.float32).astype(np.float64))
+    with pytest.raises(deg.DegError):
+        deg.knn_exact(torch.from_numpy(base).cuda(), torch.from_numpy(q).cuda(), 1025)

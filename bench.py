@@ -209,6 +209,32 @@ def time_steps(fn, steps, warmup, stream):
     return [s.elapsed_time(e) for s, e in zip(starts, ends)]
 
 
+def kernel_ms(idx, fn, steps, stream):
+    """Per-step time of the search kernels alone: events the library records on the stream just
+    before its main search kernel (after any entry routing) and just after its second kernel."""
+    import torch
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in pairs:                                     # torch creates an event at its first record
+        a.record(stream)
+        b.record(stream)
+    for a, b in pairs:
+        idx.set_kernel_timer(a, b)
+        fn()
+    idx.set_kernel_timer(None, None)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in pairs]
+
+
+def pick_eps_by(run, target=TARGET_RECALL, grid=EPS_GRID):
+    """Smallest eps of the grid whose recall run(eps) reaches the target (and that recall)."""
+    r = 0.0
+    for eps in grid:
+        r = run(eps)
+        if r >= target:
+            return eps, r
+    return grid[-1], r
+
+
 def cpu_baseline(base, adj, queries, entry, eps, budget_s=15.0):
     """The oracle as it stands, on the host cores, over a bounded sample of the queries."""
     import oracle
@@ -387,6 +413,96 @@ def serving(deg, idx, w, q, gt):
     return out
 
 
+def explore_truth(deg, bq, v, k):
+    """Exact k-NN of x_v over V without v (the exploration protocol's ground truth): k + 1
+    neighbours by knn_exact, v removed."""
+    import torch
+    ids = deg.knn_exact(bq, bq[torch.from_numpy(v).long().cuda()], k + 1)[0].cpu().numpy()
+    keep = ids != v[:, None]
+    return np.stack([row[m][:k] for row, m in zip(ids, keep)])
+
+
+def more_points(deg, idx, w, qd, bq, forms_used, stream, steps=20, warmup=3):
+    """The 1M x 128 configuration's other operating points: vector queries at k = 1 and k = 100,
+    10,000 indexed exploration queries at k = 100 (seed = the query's own vertex, never returned),
+    and the paper's exploration protocol, k = 1,000 with recall@1000 (Sec. 6.7). Each point runs
+    at the smallest eps of the grid reaching recall@k >= 0.95, timed over `steps` batches."""
+    import torch
+    out = {}
+    gt100 = deg.knn_exact(bq, qd, 100)[0].cpu().numpy()
+
+    def timed(fn, nq, eps, rec, tr):
+        ms = time_steps(fn, steps, warmup, stream)
+        m = sum(ms) / len(ms)
+        return {"qps": nq / (m / 1e3), "ms_per_step": m, "eps": eps, "recall": rec,
+                "H_mean": float(tr[:, 0].float().mean()), "E_mean": float(tr[:, 1].float().mean())}
+
+    for k in (1, 100):
+        for name, form in forms_used.items():
+            f = dict(form)
+            if f.get("rerank"):
+                f["rerank"] = max(f["rerank"], k)
+            ids_o = torch.empty((len(qd), k), dtype=torch.int32, device="cuda")
+            d_o = torch.empty((len(qd), k), dtype=torch.float32, device="cuda")
+            eps, rec = pick_eps_by(lambda e: recall(idx.search(qd, k=k, eps=e, **f)[0].cpu().numpy(), gt100[:, :k]))
+            tr = idx.search(qd, k=k, eps=eps, with_trace=True, **f)[2]
+            out[f"vector k={k}, {name}"] = timed(lambda: idx.search(qd, k=k, eps=eps, out=(ids_o, d_o), **f),
+                                                 len(qd), eps, rec, tr)
+            log(f"[bench] vector k={k}, {name}: {out[f'vector k={k}, {name}']}")
+    v = w.explore_ids()
+    vd = torch.from_numpy(v).cuda()
+    for k in (100, 1000):
+        truth = explore_truth(deg, bq, v, k)
+        for name, prec in (("float32", dict(precision="f32")), ("fp8 + re-rank", dict(precision="fp8", rerank=k))):
+            ids_o = torch.empty((len(v), k), dtype=torch.int32, device="cuda")
+            d_o = torch.empty((len(v), k), dtype=torch.float32, device="cuda")
+            run = lambda e: recall(idx.search(seeds=vd, explore=True, k=k, eps=e, **prec)[0].cpu().numpy(), truth)
+            eps, rec = pick_eps_by(run, grid=[e for e in EPS_GRID if e <= 0.2])
+            tr = idx.search(seeds=vd, explore=True, k=k, eps=eps, with_trace=True, **prec)[2]
+            key = f"exploration k={k}, {name}"
+            out[key] = timed(lambda: idx.search(seeds=vd, explore=True, k=k, eps=eps, out=(ids_o, d_o), **prec),
+                             len(v), eps, rec, tr)
+            out[key]["queries"] = len(v)
+            log(f"[bench] {key}: {out[key]}")
+    return out
+
+
+def precision_report(idx, base, q, qd, dim, eps, sample=200):
+    """Distance error of the reduced-precision stores against FP64 (Sec. 6 workloads stored in
+    bf16 and FP8-E4M3 with a per-row float32 scale): the distances the search kernel computes on
+    the stored codes (float32 accumulation, no re-rank) for its own result lists, against the FP64
+    distance to the float32 rows. Also the bound the formats' mantissa widths give for the
+    storage part: |delta_stored - delta| <= |x - decode(x)| <= 2^-9 |x| (bf16) and
+    2^-4 |x| + 2^-10 s sqrt(dim) (E4M3, subnormal spacing 2^-9 s)."""
+    import torch
+    out = {}
+    qs = q[:sample].astype(np.float64)
+    for prec in ("bf16", "fp8"):
+        ids, d = idx.search(qd[:sample], k=64, eps=eps, precision=prec, rerank=-1, entry="pivot")
+        ids, d = ids.cpu().numpy(), d.cpu().numpy().astype(np.float64)
+        if prec == "bf16":
+            codes = idx.export_codes("bf16")
+            dec = (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+            scale = np.ones(len(base))
+        else:
+            codes, scale = idx.export_codes("fp8")
+            dec = torch.from_numpy(codes).view(torch.float8_e4m3fn).float().numpy().astype(np.float64)
+            scale = scale.astype(np.float64)
+        x = base[ids].astype(np.float64)                              # [sample][64][dim]
+        xs = dec[ids] * scale[ids][..., None]
+        exact = np.sqrt(((x - qs[:, None, :]) ** 2).sum(-1))
+        store_err = np.sqrt(((x - xs) ** 2).sum(-1))
+        xn = np.sqrt((x ** 2).sum(-1))
+        bound = 2.0 ** -9 * xn if prec == "bf16" else 2.0 ** -4 * xn + 2.0 ** -10 * scale[ids] * np.sqrt(dim)
+        rel = np.abs(d - exact) / np.maximum(exact, 1e-30)
+        out[prec] = {"pairs": int(rel.size), "max_rel_err": float(rel.max()), "p99_rel_err": float(np.percentile(rel, 99)),
+                     "mean_rel_err": float(rel.mean()),
+                     "storage_err_over_bound_max": float((store_err / np.maximum(bound, 1e-30)).max()),
+                     "what": "kernel distance (stored codes, float32 accumulation, no re-rank) vs FP64 on the "
+                             "float32 rows, over each sampled query's 64 results"}
+    return out
+
+
 # eps at which the plain float32 search reaches recall@10 >= 0.95 on this workload (from the
 # sweep the GPU arm runs at start-up; the reference arm uses it so both arms do the same work)
 OPERATING_EPS = 0.08
@@ -426,6 +542,9 @@ def main():
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the k = 1 / 100 and exploration points")
+    ap.add_argument("--builder", default="host", choices=["host", "device"],
+                    help="graph builder when the workload's graph file is missing")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
                     help="workload of the form table (the headline is the default)")
@@ -458,7 +577,7 @@ def main():
     w = workload(args)
     t0 = time.time()
     base, q = w.base(), w.queries()
-    idx = graphs.load_or_build(w, base)
+    idx = graphs.load_or_build(w, base, builder=args.builder)
     idx.upload(("f32", "bf16", "fp8"))
     n, dim, degree = idx.info()
     log(f"[bench] index {n} x {dim}, d={degree}, entry {idx.entry_vertex}, setup {time.time() - t0:.1f} s")
@@ -501,11 +620,14 @@ def main():
             clocks.start()
         ms = time_steps(lambda: idx.search(qd, k=K, eps=eps, out=out, **form), steps, warmup, stream)
         clk = clocks.stop() if clocks else None
+        kms = kernel_ms(idx, lambda: idx.search(qd, k=K, eps=eps, out=out, **form), min(steps, 100), stream)
         total, qps = job_totals(sum(ms), world, len(q), steps, dist, "cuda")
         mean_ms = total / steps
+        kernel_mean = sum(kms) / len(kms)
         res = {"qps": qps, "eps": eps, "recall_at_10": rec, "ms_per_step": mean_ms,
                "p50_ms": sorted(ms)[len(ms) // 2], "p99_ms": sorted(ms)[min(len(ms) - 1, int(0.99 * len(ms)))],
                "alg_bytes": alg, "achieved_gbs": alg / (mean_ms / 1e3) / 1e9,
+               "kernel_ms": kernel_mean, "kernel_gbs": alg / (kernel_mean / 1e3) / 1e9,
                "H_mean": float(trace[:, 0].mean()), "H_max": int(trace[:, 0].max()), "E_mean": float(trace[:, 1].mean()),
                "second_kernel_frac": float(trace[:, 3].mean())}
         log(f"[bench] {name}: {res['qps']:.0f} QPS at recall {rec:.4f} (eps {eps}), {mean_ms:.2f} ms/step")
@@ -527,15 +649,46 @@ def main():
     wts, hist = deg.train_stop_model(feats[mask].contiguous(), labels[mask].contiguous(), epochs=4, batch=8192)
     log(f"[bench] stop model: {int(mask.sum())} samples, loss {[round(h, 4) for h in hist]}")
     del feats, labels, counts, mask, tq
-    idx.set_stop_model(wts, 0.7)
-    lname = base_name + ", learned stop (P>0.7)"
-    FORMS[lname] = dict(FORMS[base_name], learned_stop=True)
-    forms[lname], _ = measure(lname, FORMS[lname], max(3, args.steps // 4), args.warmup)
+    # the stop threshold is chosen like eps: every threshold with the smallest eps (from the base
+    # form's) that keeps recall@10 >= 0.95, timed briefly; the fastest pair is measured in full
+    lf = dict(FORMS[base_name], learned_stop=True)
+    grid = [e for e in EPS_GRID if e >= forms[base_name]["eps"]][:12]
+    cands = []
+    for th in (0.5, 0.6, 0.7, 0.8, 0.9):
+        idx.set_stop_model(wts, th)
+        e_th, r_th = pick_eps_by(lambda e: recall(idx.search(qd, k=K, eps=e, **lf)[0].cpu().numpy(), gt), grid=grid)
+        if r_th >= TARGET_RECALL:
+            ms = time_steps(lambda: idx.search(qd, k=K, eps=e_th, out=out, **lf), 20, 3, stream)
+            cands.append((sum(ms) / len(ms), th, e_th))
+            log(f"[bench] learned stop P>{th}: eps {e_th}, recall {r_th:.4f}, {sum(ms) / len(ms):.3f} ms")
+    if cands:
+        _, th, e_th = min(cands)
+        idx.set_stop_model(wts, th)
+        lname = base_name + f", learned stop (P>{th})"
+        FORMS[lname] = lf
+        forms[lname], _ = measure(lname, lf, max(3, args.steps // 4), args.warmup)
+        # queries the network ended before the eps rule would have, at that eps
+        _, _, tr_l = idx.search(qd, k=K, eps=forms[lname]["eps"], with_trace=True, **lf)
+        _, _, tr_p = idx.search(qd, k=K, eps=forms[lname]["eps"], with_trace=True, **FORMS[base_name])
+        forms[lname]["stopped_early_frac"] = float((tr_l[:, 0] < tr_p[:, 0]).float().mean())
+        forms[lname]["threshold_sweep"] = [{"threshold": t, "eps": e, "ms": m} for m, t, e in cands]
     ok = {k: v for k, v in forms.items() if v["recall_at_10"] >= TARGET_RECALL}
     best = max(ok or forms, key=lambda k: (ok or forms)[k]["qps"])
     # the headline: the fastest form, timed again over the full step count with clocks sampled
     head, clk = measure(best, FORMS[best], args.steps, args.warmup, clocks)
     eps = head["eps"]
+
+    extra = {}
+    if not args.no_extra and w.name == WORKLOAD:
+        used = {"plain float32, fixed entry": FORMS["plain float32, fixed entry"], best: FORMS[best]}
+        extra = more_points(deg, idx, w, qd, torch.from_numpy(base).cuda(), used, stream)
+    precision = precision_report(idx, base, q, qd, dim, forms[best]["eps"])
+    # recall at one eps for the three stores (the recall loss of the reduced precisions)
+    same_eps = {}
+    for pname in ("f32", "bf16", "fp8"):
+        f = dict(precision=pname, entry="pivot") if pname == "f32" else dict(precision=pname, rerank=args.rerank, entry="pivot")
+        same_eps[pname] = recall(idx.search(qd, k=K, eps=forms[best]["eps"], **f)[0].cpu().numpy(), gt)
+    precision["recall_at_10_same_eps"] = {"eps": forms[best]["eps"], **same_eps}
 
     # end to end through the C ABI with host buffers (H2D of the queries, D2H of the results)
     qh = torch.from_numpy(q).pin_memory().numpy()
@@ -554,10 +707,13 @@ def main():
     peak, peak_kind = measured_peak()
 
     def roofline(r, kernel, traffic):
-        return {"bound": "hbm", "achieved": r["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                "frac": r["achieved_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
-                "alg_bytes_per_launch": r["alg_bytes"],
-                "timed_over": "the whole search call (entry routing included), not the kernel alone",
+        return {"bound": "hbm", "achieved": r["kernel_gbs"], "peak": peak, "unit": "GB/s",
+                "frac": r["kernel_gbs"] / peak, "traffic": traffic, "peak_kind": peak_kind, "kernel": kernel,
+                "alg_bytes_per_launch": r["alg_bytes"], "kernel_ms": r["kernel_ms"],
+                "timed_over": "the search kernels alone (main + second kernel), CUDA events the library records "
+                              "on the launching stream around their launches",
+                "call": {"ms": r["ms_per_step"], "achieved": r["achieved_gbs"], "frac": r["achieved_gbs"] / peak,
+                         "what": "the whole search call, entry routing included"},
                 "per_query": {"H_mean": r["H_mean"], "H_max": r["H_max"], "E_mean": r["E_mean"],
                               "second_kernel_frac": r["second_kernel_frac"]}}
 
@@ -584,6 +740,8 @@ def main():
         "roofline_plain_fp32": roofline(plain, "search_fast_kernel (F32Rows, 32 lanes/row)",
                                         recorded_traffic("plain", plain["eps"], w.name)),
         "knn_exact": knn_line(knn_ms, len(q), n, dim),
+        "precision": precision,
+        "other_points": extra,
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},
         # per step: routing (query bf16 copy, two tensor-core passes, limit, finish, ids and work

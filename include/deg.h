@@ -89,18 +89,33 @@ DEG_API deg_status deg_build(const float* base_host, int64_t n, int32_t dim, con
  * (at least 1, at most 8,192), so the vertices of a batch rarely fall in each other's
  * neighbourhoods; old vertices are claimed per batch, so two new vertices never rewire the same
  * vertex in one batch, and a vertex that runs out of free candidates is inserted again later with
- * more candidates. The optional optimizeEdge step of Alg. 3 (k_opt, eps_opt, i_opt) and
- * refine_rounds are not applied: the result is the paper's construction-only graph (App. G). The
- * graph is an even-regular, symmetric, connected graph without loops or duplicates (checked
- * before returning; DEG_EGRAPH otherwise), but not the graph the sequential builder makes: which
- * new vertex claims an old vertex first depends on the order the warps run in. Copies the vectors;
- * device memory about n * (4 dim + 12 degree) bytes plus the search scratch, all freed before
- * returning. Synchronises `stream`. DEG_EINVAL when dim is outside 1 ... 1024, degree is odd or
- * outside 4 ... 128, n < degree + 1 or above 2^31 - 1, k_ext is outside degree ... 1024, eps_ext
- * < 0 or batch_div < 1; DEG_ECUDA on a device error. progress (nullable) receives the number of
- * vertices inserted so far. */
+ * more candidates. With i_opt > 0, each batch then runs the optional last line of Alg. 3,
+ * optimizeEdge (Alg. 4; k_opt, eps_opt, i_opt iterations) for every new edge (v, u) with u outside
+ * v's search result: all of a batch's optimisations at once, one per new vertex at a time, their
+ * searches batched; an optimisation claims each vertex it rewires and is undone and repeated
+ * later if another holds one. i_opt = 0 gives the paper's construction-only graph (App. G).
+ * refine_rounds > 0 then runs that many rounds of Alg. 5 (as deg_refine_device). The graph is an
+ * even-regular, symmetric, connected graph without loops or duplicates (checked before
+ * returning; DEG_EGRAPH otherwise), but not the graph the sequential builder makes: which batch
+ * member claims a vertex first depends on the order the warps run in. Copies the vectors; device
+ * memory about n * (4 dim + 12 degree) bytes plus the search scratch, all freed before returning.
+ * Synchronises `stream`. DEG_EINVAL when dim is outside 1 ... 1024, degree is odd or outside
+ * 4 ... 128, n < degree + 1 or above 2^31 - 1, k_ext is outside degree ... 1024, i_opt is outside
+ * 0 ... 6, k_opt outside 1 ... 1024 (with i_opt > 0), refine_rounds < 0 or > 0 with i_opt = 0, an
+ * eps < 0 or batch_div < 1; DEG_ECUDA on a device error. progress (nullable) receives the number
+ * of vertices inserted so far. */
 DEG_API deg_status deg_build_device(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
                                     int32_t batch_div, volatile int64_t* progress, deg_index** out, void* stream);
+
+/* dynamicEdgeOptimization (Sec. 5.3, Alg. 5) on the current GPU over the index's graph:
+ * p->refine_rounds rounds, each taking a random vertex v1 (SplitMix64 from p->seed) and running
+ * optimizeEdge (Alg. 4; p->i_opt, p->k_opt, p->eps_opt) on each edge (v1, v2) that fails
+ * checkMRNG (Alg. 2) and then on v1's longest edge. Up to 4,096 rounds run at once, on distinct
+ * vertices, with the same claims as deg_build_device; so the rounds are not the sequential
+ * order's. The graph keeps its invariants (checked; DEG_EGRAPH otherwise). *improved (nullable)
+ * receives the number of optimisations that changed the graph. The host adjacency is replaced and
+ * the device copy released: upload again before searching. p->degree must equal the index's. */
+DEG_API deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
 
 /* Wrap an existing graph: base_host [n][dim] float32 and adj_host [n][degree] int32 are copied.
  * The adjacency is checked (every entry in [0,n), no self-loops, no duplicates, symmetric,
@@ -144,7 +159,9 @@ typedef struct {
     float eps;            /* range factor eps >= 0 of Alg. 1                                  */
     int32_t precision;    /* DEG_F32 | DEG_BF16 | DEG_FP8 (the copy must have been uploaded)  */
     int32_t rerank;       /* precision != F32: keep this many candidates (>= k, <= 1024) and
-                             re-rank them on the float32 rows; 0 = k (no widening)           */
+                             re-rank them on the float32 rows; 0 = k (no widening); -1 = no
+                             re-rank: the k results and distances of the reduced-precision
+                             search as computed (to measure the format's distance error)     */
     int32_t max_hops;     /* 0 = unlimited; else a query stops after this many expansions and
                              reports DEG_EHOPLIMIT with its current result list               */
     int32_t visited_cap;  /* reserved, must be 0 (the checked set is an n-bit bitmap)          */
@@ -154,9 +171,10 @@ typedef struct {
     int32_t entry_mode;   /* plain searches with no seeds: 0 = the fixed entry vertex (paper,
                              Sec. 5.4); 1 = per query, the nearest of the index's pivot vertices
                              (about n/256, at most 4096, chosen at upload) -- not in the paper */
-    int32_t learned_stop; /* 1: after every hop the index's stop network (deg_set_stop_model)
-                             may end the search early; the eps test still applies. Not in the
-                             paper; 0 = the plain method */
+    int32_t learned_stop; /* 1: every fourth hop, once R has not changed for two hops, the
+                             index's stop network (deg_set_stop_model) may end the search
+                             early; the eps test still applies. Not in the paper; 0 = the
+                             plain method */
 } deg_search_params;
 
 /* Plain search: one Alg. 1 run per query q of queries_dev [nq][dim] float32, seeded at

@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         sig = {
             "deg_build": (S, [P, i64, i32, ctypes.POINTER(BuildParams), P, ctypes.POINTER(P)]),
             "deg_build_device": (S, [P, i64, i32, ctypes.POINTER(BuildParams), i32, P, ctypes.POINTER(P), P]),
+            "deg_refine_device": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -153,15 +154,24 @@ class Index:
         return cls(h)
 
     @classmethod
-    def build_device(cls, base: np.ndarray, degree: int, k_ext: int, eps_ext: float, batch_div: int = 256,
-                     stream=None) -> "Index":
-        """ExtendGraph in batches on the current GPU (deg_build_device); no edge optimisation."""
+    def build_device(cls, base: np.ndarray, degree: int, k_ext: int, eps_ext: float, k_opt: int = 0,
+                     eps_opt: float = 0.001, i_opt: int = 0, refine_rounds: int = 0, seed: int = 0,
+                     batch_div: int = 256, stream=None) -> "Index":
+        """ExtendGraph in batches on the current GPU (deg_build_device), with optimizeEdge when i_opt > 0."""
         base = np.ascontiguousarray(base, np.float32)
-        p = BuildParams(degree, k_ext, eps_ext, degree, 0.001, 0, 0, 0)
+        p = BuildParams(degree, k_ext, eps_ext, k_opt or degree, eps_opt, i_opt, refine_rounds, seed)
         h = ctypes.c_void_p()
         _check(lib().deg_build_device(base.ctypes.data, base.shape[0], base.shape[1], ctypes.byref(p), batch_div, None,
                                       ctypes.byref(h), _stream_ptr(stream)))
         return cls(h)
+
+    def refine_device(self, rounds: int, k_opt: int, eps_opt: float, i_opt: int, seed: int = 0, stream=None) -> int:
+        """Alg. 5 for `rounds` random vertices on the GPU (deg_refine_device); returns the improved count."""
+        _, _, degree = self.info()
+        p = BuildParams(degree, degree, 0.2, k_opt, eps_opt, i_opt, rounds, seed)
+        improved = ctypes.c_int64()
+        _check(lib().deg_refine_device(self._h, ctypes.byref(p), ctypes.byref(improved), _stream_ptr(stream)))
+        return improved.value
 
     @classmethod
     def from_arrays(cls, base: np.ndarray, adj: np.ndarray) -> "Index":

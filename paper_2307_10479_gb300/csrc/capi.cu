@@ -168,7 +168,10 @@ extern "C" deg_status deg_build_device(const float* base_host, int64_t n, int32_
     if (n < p->degree + 1) return fail(DEG_EINVAL, "deg_build_device: need n >= degree + 1");
     if (n > INT32_MAX) return fail(DEG_EINVAL, "deg_build_device: n must fit in int32");
     if (p->k_ext < p->degree || p->k_ext > 1024) return fail(DEG_EINVAL, "deg_build_device: need degree <= k_ext <= 1024");
-    if (!(p->eps_ext >= 0.f)) return fail(DEG_EINVAL, "deg_build_device: eps_ext must be >= 0");
+    if (p->i_opt < 0 || p->i_opt > 6 || (p->i_opt > 0 && (p->k_opt < 1 || p->k_opt > 1024)) || p->refine_rounds < 0)
+        return fail(DEG_EINVAL, "deg_build_device: need 0 <= i_opt <= 6, 1 <= k_opt <= 1024, refine_rounds >= 0");
+    if (p->refine_rounds > 0 && p->i_opt == 0) return fail(DEG_EINVAL, "deg_build_device: refine_rounds needs i_opt >= 1");
+    if (!(p->eps_ext >= 0.f) || !(p->eps_opt >= 0.f)) return fail(DEG_EINVAL, "deg_build_device: eps must be >= 0");
     if (batch_div < 1) return fail(DEG_EINVAL, "deg_build_device: batch_div must be >= 1");
     deg_index* idx = new_index(n, dim, p->degree);
     if (!idx) return fail(DEG_ENOMEM, "deg_build_device: host allocation failed");
@@ -186,6 +189,26 @@ extern "C" deg_status deg_build_device(const float* base_host, int64_t n, int32_
         return s;
     }
     *out = idx;
+    return DEG_OK;
+}
+
+extern "C" deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream) {
+    if (!idx || !p) return fail(DEG_EINVAL, "deg_refine_device: NULL argument");
+    if (p->degree != idx->degree) return fail(DEG_EINVAL, "deg_refine_device: params.degree differs from the index's");
+    if (idx->degree > 128) return fail(DEG_EINVAL, "deg_refine_device: degree above 128");
+    if (p->refine_rounds < 0 || p->i_opt < 1 || p->i_opt > 6 || p->k_opt < 1 || p->k_opt > 1024 || !(p->eps_opt >= 0.f))
+        return fail(DEG_EINVAL, "deg_refine_device: need refine_rounds >= 0, 1 <= i_opt <= 6, 1 <= k_opt <= 1024, eps_opt >= 0");
+    if (p->refine_rounds == 0) {
+        if (improved) *improved = 0;
+        return DEG_OK;
+    }
+    std::string why;
+    const int e = refine_graph_device(idx->x.data(), idx->adj.data(), idx->n, idx->dim, *p, idx->adj.data(), improved,
+                                      static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "deg_refine_device: " + why);
+    const deg_status s = check_graph(idx->adj.data(), idx->n, idx->degree);
+    if (s != DEG_OK) return s;
+    free_device(idx);                                          // the device copy shows the old graph
     return DEG_OK;
 }
 
@@ -393,8 +416,8 @@ deg_status validate_search(const deg_index* idx, const deg_search_params* p, con
     if (!(p->eps >= 0.f) || std::isinf(p->eps)) return fail(DEG_EINVAL, "search: eps must be finite and >= 0");
     if (p->precision < DEG_F32 || p->precision > DEG_FP8) return fail(DEG_EINVAL, "search: unknown precision");
     if (!(idx->uploaded_mask & (1 << p->precision))) return fail(DEG_ENOTREADY, "search: precision copy not uploaded");
-    if (p->rerank < 0 || p->rerank > 1024 || (p->rerank && p->rerank < p->k))
-        return fail(DEG_EINVAL, "search: rerank must be 0 or in [k, 1024]");
+    if (p->rerank < -1 || p->rerank > 1024 || (p->rerank > 0 && p->rerank < p->k))
+        return fail(DEG_EINVAL, "search: rerank must be -1, 0 or in [k, 1024]");
     if (p->max_hops < 0) return fail(DEG_EINVAL, "search: max_hops must be >= 0");
     if (p->visited_cap != 0) return fail(DEG_EINVAL, "search: visited_cap is reserved and must be 0");
     if (p->queue_cap < 0 || p->queue_cap > 32768) return fail(DEG_EINVAL, "search: queue_cap must be in [0, 32768]");

@@ -24,6 +24,10 @@ int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& 
 // [n][degree] written to adj_out (host). Returns a cudaError_t value (0 = success).
 int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,
                        int32_t* adj_out, volatile int64_t* progress, deg_stream_t stream, std::string* why);
+// Alg. 5 (p.refine_rounds rounds, p.i_opt / k_opt / eps_opt, SplitMix64(p.seed)) on the device over
+// an existing graph adj_in [n][degree]; the result goes to adj_out (may be adj_in).
+int refine_graph_device(const float* x_host, const int32_t* adj_in, int64_t n, int32_t dim, const deg_build_params& p,
+                        int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why);
 
 // Record an error message for deg_last_error() and return the status.
 deg_status fail(deg_status s, const std::string& msg);

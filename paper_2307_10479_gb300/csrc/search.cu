@@ -46,7 +46,10 @@ namespace deg {
 namespace {
 
 constexpr int kWarpsPerBlock = 4;
-constexpr int kBlocksPerSM = 6;          // occupancy target: 24 warps per SM (85 registers)
+#ifndef DEG_SEARCH_BLOCKS_PER_SM
+#define DEG_SEARCH_BLOCKS_PER_SM 6
+#endif
+constexpr int kBlocksPerSM = DEG_SEARCH_BLOCKS_PER_SM;   // occupancy target: 24 warps per SM (85 registers)
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxDegree = 128;
 constexpr int kFront = 128;              // sorted on-chip part of S
@@ -916,7 +919,10 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         W.peak = max(W.peak, W.fn + W.back_n);
         __syncwarp();
-        if (P.learned || P.rec_feats) {
+        // the learned stop is asked every fourth hop, and only once R has not changed for two hops
+        // (while R still changes, more expansion is evidently still paying)
+        const bool ask = P.learned && (W.hops & 3) == 0 && W.hops - W.last_change >= 2;
+        if (ask || P.rec_feats) {
             float x[kStopFeatures];
 #pragma unroll
             for (int i = 0; i < kStopFeatures; ++i) x[i] = stop_feature(W, i, key_d2(m), cnt, adm, P.f);
@@ -926,8 +932,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
                 for (int i = 1; i < kStopFeatures; ++i) v = lane == i ? x[i] : v;
                 P.rec_feats[((int64_t)q * P.rec_cap + (W.hops - 1)) * kStopFeatures + lane] = v;
             }
-            // learned stop, evaluated every other hop (the network costs about as much as a hop)
-            if (P.learned && (W.hops & 1) == 0 && stop_margin(P.stop_w, x, lane) > P.stop_logit) break;
+            if (ask && stop_margin(P.stop_w, x, lane) > P.stop_logit) break;
         }
     }
     finish_query(P, W, q, qv_smem, status, tier, lane);
@@ -1336,9 +1341,9 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.nq = (int32_t)a.nq;
     P.k = a.k;
     const bool reduced = a.precision != DEG_F32;
-    P.ks = reduced && a.rerank ? std::max(a.rerank, a.k) : a.k;
+    P.ks = reduced && a.rerank > 0 ? std::max(a.rerank, a.k) : a.k;
     P.kcap = std::max(32, pow2_at_least(P.ks));
-    P.rerank = reduced ? 1 : 0;
+    P.rerank = reduced && a.rerank >= 0 ? 1 : 0;             // -1: the reduced-precision distances as computed
     const float2 fe = eps_factor(a.eps);
     P.f = fe.x;
     P.f_lo = fe.y;

@@ -1,12 +1,14 @@
-"""Graph construction on the device (batched ExtendGraph, Alg. 3 scheme C with RNG checks).
+"""Graph construction on the device: batched ExtendGraph (Alg. 3, scheme C with RNG checks),
+batched optimizeEdge (Alg. 4) for the new edges, and batched dynamicEdgeOptimization (Alg. 5).
 
-The device builder makes a different graph than the sequential oracle (batches, claims, no edge
-optimisation), so it is held to what both must satisfy and to search quality:
+The device builder makes a different graph than the sequential oracle (batches, claims, the order
+the warps run in), so it is held to what both must satisfy and to search quality:
 - the structural invariants of the paper's graphs, checked by the oracle: every vertex has
-  exactly d neighbours, the adjacency is symmetric, no loops or duplicates, BFS-connected (on a
-  small graph also bridge-free, App. B's 2-edge connectivity);
-- Alg. 1 on the device-built graph reaches the recall of Alg. 1 on the oracle's graph within a
-  stated margin at the same eps (both searched by the oracle, FP64);
+  exactly d neighbours, the adjacency is symmetric, no loops or duplicates, BFS-connected (on the
+  smallest graphs also bridge-free, App. B's 2-edge connectivity);
+- Alg. 1 on the device-built graph reaches the recall of Alg. 1 on the sequential oracle's graph
+  within 0.02 at the same eps (both searched by the oracle, FP64), with and without optimizeEdge;
+- Alg. 5 lowers the average neighbour distance it minimises (Sec. 5.3) and keeps the invariants;
 - the library's search on the device-built graph is the oracle's search on it (parity)."""
 import numpy as np
 import pytest
@@ -21,32 +23,38 @@ pytestmark = pytest.mark.gpu
 W = synth.WORKLOADS["uniform-10k-d32"]
 
 
+def _params(i_opt):
+    return dict(k_opt=W.k_opt, eps_opt=W.eps_opt, i_opt=i_opt)
+
+
 @pytest.fixture(scope="module")
 def built():
     import paper_2307_10479_gb300 as deg
     base, q = W.base(), W.queries()
-    idx = deg.Index.build_device(base, W.degree, W.k_ext, W.eps_ext)
-    adj = idx.adjacency()
+    full = deg.Index.build_device(base, W.degree, W.k_ext, W.eps_ext, **_params(W.i_opt))
+    plain = deg.Index.build_device(base, W.degree, W.k_ext, W.eps_ext, **_params(0))
     gt, _ = oracle.knn_bruteforce(base, q, 10)
-    return dict(deg=deg, base=base, q=q, idx=idx, adj=adj, gt=gt)
+    return dict(deg=deg, base=base, q=q, idx=full, adj=full.adjacency(), adj0=plain.adjacency(), gt=gt)
 
 
 def test_device_graph_invariants(built):
-    adj = built["adj"]
-    assert adj.shape == (W.n, W.degree)
-    assert oracle.check_graph(adj) == 0
+    for adj in (built["adj"], built["adj0"]):
+        assert adj.shape == (W.n, W.degree)
+        assert oracle.check_graph(adj) == 0
 
 
-def test_device_graph_search_quality_against_the_oracle_graph(built):
+@pytest.mark.parametrize("i_opt", [0, 5])
+def test_device_graph_search_quality_against_the_oracle_graph(built, i_opt):
+    # the sequential oracle's graph with the same parameters; i_opt = 0 leaves out the optional
+    # optimizeEdge of Alg. 3 on both sides (the paper's construction-only graph)
     base, q, gt = built["base"], built["q"], built["gt"]
-    # the sequential oracle's construction-only graph (i_opt = 0: the optional optimizeEdge of
-    # Alg. 3 never changes an edge), the same algorithm the device runs in batches
-    o_adj = oracle.build_graph(base, W.degree, W.k_ext, W.eps_ext, W.k_opt, W.eps_opt, 0)
+    g_adj = built["adj"] if i_opt else built["adj0"]
+    o_adj = oracle.build_graph(base, W.degree, W.k_ext, W.eps_ext, W.k_opt, W.eps_opt, i_opt)
     entry = np.full(len(q), oracle.median_vertex(base), np.int32)
     for eps in (0.1, 0.2):
-        g_ids, _, g_tr = oracle.range_search(base, built["adj"], q, entry, 10, eps)
+        g_ids, _, g_tr = oracle.range_search(base, g_adj, q, entry, 10, eps)
         o_ids, _, o_tr = oracle.range_search(base, o_adj, q, entry, 10, eps)
-        print(f"eps {eps}: device {recall(g_ids, gt):.4f} ({g_tr[:, 1].mean():.0f} evals), "
+        print(f"i_opt {i_opt} eps {eps}: device {recall(g_ids, gt):.4f} ({g_tr[:, 1].mean():.0f} evals), "
               f"sequential {recall(o_ids, gt):.4f} ({o_tr[:, 1].mean():.0f} evals)")
         assert recall(g_ids, gt) >= recall(o_ids, gt) - 0.02, (eps, recall(g_ids, gt), recall(o_ids, gt))
 
@@ -60,14 +68,31 @@ def test_search_parity_on_the_device_graph(built):
     compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d)
 
 
-@pytest.mark.parametrize("degree,batch_div", [(30, 256), (30, 2), (8, 1)])
-def test_invariants_under_heavy_contention(degree, batch_div):
+def test_refinement_lowers_the_average_neighbour_distance(built):
+    deg, base = built["deg"], built["base"]
+    idx = deg.Index.from_arrays(base, built["adj0"])
+    before = oracle.average_neighbor_distance(base, built["adj0"])
+    improved = idx.refine_device(20_000, W.k_opt, W.eps_opt, W.i_opt, seed=11)
+    adj = idx.adjacency()
+    after = oracle.average_neighbor_distance(base, adj)
+    print(f"Alg. 5, 20,000 rounds: {improved} edges improved, AND {before:.5f} -> {after:.5f}")
+    assert oracle.check_graph(adj) == 0
+    assert improved > 0 and after < before
+    idx.upload()                                              # the refined graph searches as usual
+    ids, _ = idx.search(torch.from_numpy(built["q"][:64]).cuda(), k=10, eps=0.1)
+    assert (ids.cpu().numpy() >= 0).all()
+
+
+@pytest.mark.parametrize("degree,batch_div,i_opt", [(30, 256, 5), (30, 2, 5), (8, 1, 5), (8, 1, 0)])
+def test_invariants_under_heavy_contention(degree, batch_div, i_opt):
     # batch_div 1-2: a batch as large as half the graph, so new vertices compete for the same old
-    # vertices and some run out of candidates and are inserted again later
+    # vertices and some run out of candidates and are inserted again later; their optimisations
+    # compete too and some are undone and repeated
     import paper_2307_10479_gb300 as deg
     w = synth.scaled(synth.WORKLOADS["sift-1m-d128"], 6_000, 10)
     base = w.base()
-    idx = deg.Index.build_device(base, degree, 2 * degree, 0.2, batch_div=batch_div)
+    idx = deg.Index.build_device(base, degree, 2 * degree, 0.2, k_opt=degree, eps_opt=0.001, i_opt=i_opt,
+                                 batch_div=batch_div)
     adj = idx.adjacency()
     assert oracle.check_graph(adj, bridge_max_n=6_000 if degree == 8 else 0) == 0
 
@@ -78,8 +103,9 @@ def test_smallest_graphs_and_bad_arguments():
     adj = deg.Index.build_device(base[:9], 8, 8, 0.2).adjacency()       # K_9 itself
     assert oracle.check_graph(adj) == 0
     assert all(set(adj[u]) == set(range(9)) - {u} for u in range(9))
-    assert oracle.check_graph(deg.Index.build_device(base, 8, 8, 0.2).adjacency()) == 0
-    for kw in (dict(degree=7, k_ext=8), dict(degree=8, k_ext=4), dict(degree=130, k_ext=130)):
+    assert oracle.check_graph(deg.Index.build_device(base, 8, 8, 0.2, i_opt=5, k_opt=8).adjacency()) == 0
+    for kw in (dict(degree=7, k_ext=8), dict(degree=8, k_ext=4), dict(degree=130, k_ext=130),
+               dict(degree=8, k_ext=8, i_opt=7), dict(degree=8, k_ext=8, refine_rounds=5)):
         with pytest.raises(deg.DegError):
             deg.Index.build_device(synth.uniform(200, 4, 3), eps_ext=0.2, **kw)
     with pytest.raises(deg.DegError):

@@ -52,11 +52,48 @@ def test_reduced_precision_search_parity(setup, precision, keep):
 
 
 def test_reduced_precision_distance_error_and_recall(setup):
-    # Report-style bounds: BF16 keeps 8 mantissa bits (|err| <= 2^-9 relative per element),
-    # FP8 3 bits; with a 64-wide re-rank the recall loss against float32 stays small.
-    idx, gt = setup["idx"], setup["gt"]
+    # The distances the kernel computes on the stored codes (rerank=-1: no re-rank) against FP64
+    # on the float32 rows, pair by pair, within the bound the formats and float32 give:
+    #   |d_kernel - delta| <= |x - s decode(x)|                  (storage, triangle inequality)
+    #                        + float32 accumulation of the kernel's sum,
+    # and the storage term within the mantissa widths: 2^-9 |x| for bf16 (8 significant bits,
+    # round to nearest), 2^-4 |x| + 2^-10 s sqrt(dim) for E4M3 (4 significant bits, subnormal
+    # spacing 2^-9 s). The accumulation term: bf16 sums (q - x)^2 directly, relative error at most
+    # (dim + 8) 2^-24 of the distance; FP8 expands |q|^2 - 2 s q.x + s^2 |x|^2, absolute error of
+    # the square at most (dim + 8) 2^-24 (|q| + s |x|)^2, so of the distance at most its root.
+    idx, gt, base, q = setup["idx"], setup["gt"], setup["base"], setup["q"]
+    dim = base.shape[1]
+    u = 2.0 ** -24 * (dim + 8)
+    qs = q.astype(np.float64)
     f_ids, _ = idx.search(setup["qd"], k=10, eps=0.1)
     r32 = recall(f_ids.cpu().numpy(), gt)
     for precision in ("bf16", "fp8"):
-        ids, _ = idx.search(setup["qd"], k=10, eps=0.1, precision=precision, rerank=64)
-        assert recall(ids.cpu().numpy(), gt) >= r32 - 0.05
+        ids, d = idx.search(setup["qd"], k=10, eps=0.1, precision=precision, rerank=-1)
+        ids, d = ids.cpu().numpy(), d.cpu().numpy().astype(np.float64)
+        if precision == "bf16":
+            xs = oracle.decode("bf16", oracle.quantize_bf16(base)).astype(np.float64)
+            s = np.ones(len(base))
+        else:
+            codes, sc = oracle.quantize_fp8(base)
+            xs = oracle.decode("fp8", codes, sc).astype(np.float64)          # s * decode(x)
+            s = sc.astype(np.float64)
+        x = base[ids].astype(np.float64)
+        xq = xs[ids]
+        exact = np.sqrt(((x - qs[:, None, :]) ** 2).sum(-1))
+        stored = np.sqrt(((xq - qs[:, None, :]) ** 2).sum(-1))
+        store_err = np.sqrt(((x - xq) ** 2).sum(-1))
+        xn = np.sqrt((x ** 2).sum(-1))
+        fmt = 2.0 ** -9 * xn if precision == "bf16" else 2.0 ** -4 * xn + 2.0 ** -10 * s[ids] * np.sqrt(dim)
+        assert (store_err <= fmt * (1 + 1e-9)).all()
+        if precision == "bf16":
+            arith = u * stored
+        else:
+            qn = np.sqrt((qs ** 2).sum(-1))[:, None]
+            arith = np.sqrt(u) * (qn + np.sqrt((xq ** 2).sum(-1)))
+        err = np.abs(d - exact)
+        assert (err <= store_err + arith + 1e-6 * exact).all(), precision
+        rel = err / exact
+        print(f"{precision}: max relative distance error vs FP64 {rel.max():.3e} (mean {rel.mean():.3e}) "
+              f"over {rel.size} pairs")
+        r_ids, _ = idx.search(setup["qd"], k=10, eps=0.1, precision=precision, rerank=64)
+        assert recall(r_ids.cpu().numpy(), gt) >= r32 - 0.05

@@ -7,12 +7,13 @@
 //      neighbour in the visited bitmap C (one atomic per lane);
 //   3. gather the rows of the unvisited neighbours with 16-byte loads, G lanes per row and up to
 //      8 rows in flight, and reduce their squared distances with xor shuffles;
-//   4. admit to S every neighbour with d2 <= r2 (1+eps)^2 and try every neighbour with
-//      d2 <= r2 for R, both against the radius from before the hop.
-// Evaluating a hop's neighbours together and admitting against the pre-hop radius returns the
-// same R, the same expansions and the same checked set as the one-by-one loop of Alg. 1: R is
-// always the k smallest (distance, id) seen so far, and an extra candidate admitted to S with
-// the older, larger radius can only be popped when the search already stops.
+//   4. try every neighbour with d2 <= r2 for R (the radius from before the hop), keep the ks
+//      smallest; then admit to S every neighbour with d2 <= r2 (1+eps)^2 for the radius after it.
+// Evaluating a hop's neighbours together returns the same R, the same expansions and the same
+// checked set as the one-by-one loop of Alg. 1: R is always the k smallest (distance, id) seen so
+// far, and a candidate the one-by-one loop admits to S that the batch leaves out (it lies outside
+// the radius after the hop) could only ever be popped to fail the stop test -- r never grows --
+// and then the next key of S fails it too.
 //
 // Readings of Alg. 1 (as in the rest of the library): seeds count as checked; exploration
 // queries search from their own vertex but never return it; r = +inf until R first exceeds k;
@@ -899,23 +900,30 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         eng.distances(P, W.cid, W.cd2, cnt, lane);
         __syncwarp();
 
-        // 4. admit against the radius from before the hop
+        // 4. R <- R u {n : d(n) <= r} against the radius from before the hop, keeping the ks smallest
         const float r2pre = W.trimmed ? W.r2 : inf;
-        const Radius thrpre{r2pre, P.f, P.f_lo};
-        int adm = 0;
         W.hop_rins = 0;
         for (int i0 = 0; i0 < cnt; i0 += 32) {
             const int i = i0 + lane;
             const bool valid = i < cnt;
             const float d2 = valid ? W.cd2[i] : inf;
+            result_batch(W, P.ks, make_key(d2, valid ? W.ccid[i] : -1), valid && d2 <= r2pre, lane);
+        }
+        // 5. S <- S u {n : d(n) <= r (1 + eps)} against the radius after the hop: a candidate outside
+        //    it could only ever be popped to fail the stop test (r never grows), and the next key
+        //    of S would fail it as well, so leaving it out changes no pop and no result
+        const Radius thr_post{W.trimmed ? W.r2 : inf, P.f, P.f_lo};
+        int adm = 0;
+        for (int i0 = 0; i0 < cnt; i0 += 32) {
+            const int i = i0 + lane;
+            const bool valid = i < cnt;
+            const float d2 = valid ? W.cd2[i] : inf;
             const int32_t id = valid ? W.ccid[i] : -1;
-            const uint64_t key = make_key(d2, id);
-            const bool toS = valid && thrpre.admits(d2);
+            const bool toS = valid && thr_post.admits(d2);
             if (toS)  // its adjacency row is read if it is ever expanded: start pulling it into L2
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
             adm += __popc(__ballot_sync(0xffffffffu, toS));
-            if (!admit_batch(W, key, toS, thrpre, lane)) return false;
-            result_batch(W, P.ks, key, valid && d2 <= r2pre, lane);
+            if (!admit_batch(W, make_key(d2, id), toS, thr_post, lane)) return false;
         }
         W.peak = max(W.peak, W.fn + W.back_n);
         __syncwarp();

@@ -312,7 +312,8 @@ def run_reference(args, rank):
 def run_stop_sweep(args):
     """--stop-sweep WORKLOAD: the learned early stop against the plain eps rule on the paper's form
     (float32 rows, fixed entry vertex). The plain rule runs at the smallest eps (to 0.001) reaching
-    recall@10 >= 0.95. The network is trained on traces of 20,000 held-out queries at that eps; then
+    recall@10 >= 0.95. The network is trained on traces of 100,000 held-out queries at that eps (at
+    most 20M recorded hops, drawn uniformly, per epoch budget); then
     every (eps, threshold) pair from that eps upwards is searched, and the fastest pair reaching the
     recall target is timed like the plain rule. Prints one JSON line (not the headline)."""
     import torch
@@ -321,7 +322,9 @@ def run_stop_sweep(args):
     w = synth.WORKLOADS[args.stop_sweep]
     w = synth.scaled(w, args.n, w.nq) if args.n else w
     base, q = w.base(), w.queries()
-    idx = graphs.load_or_build(w, base, allow_build=False)
+    t0 = time.time()
+    idx = graphs.load_or_build(w, base, builder=args.builder)
+    build_s = time.time() - t0
     idx.upload(("f32",))
     qd = torch.from_numpy(q).cuda()
     gt = deg.knn_exact(torch.from_numpy(base).cuda(), qd, K)[0].cpu().numpy()
@@ -343,13 +346,24 @@ def run_stop_sweep(args):
     r0, e0, h0 = run(eps0, False)
     plain = {"eps": eps0, "recall_at_10": r0, "E_mean": e0, "H_mean": h0, "qps": timed(eps0, False)}
     log(f"[stop] plain eps {eps0}: recall {r0:.4f}, E {e0:.0f}, {plain['qps']:.0f} QPS")
-    tq = torch.from_numpy(w.training_queries(20000)).cuda()
+    n_train = min(100_000, args.train_queries)
     cap = 1024
-    feats, labels, counts = idx.stop_record(tq, k=K, eps=eps0, cap=cap, **form)
-    mask = torch.arange(cap, device="cuda")[None, :] < counts[:, None]
-    wts, hist = deg.train_stop_model(feats[mask].contiguous(), labels[mask].contiguous(), epochs=4, batch=8192)
-    samples = int(mask.sum())
-    del feats, labels, counts, mask, tq
+    fs, ls = [], []
+    for lo in range(0, n_train, 25_000):                   # record in slices to bound the trace memory
+        tq = torch.from_numpy(w.training_queries(n_train)[lo:lo + 25_000]).cuda()
+        feats, labels, counts = idx.stop_record(tq, k=K, eps=eps0, cap=cap, **form)
+        mask = torch.arange(cap, device="cuda")[None, :] < counts[:, None]
+        fs.append(feats[mask])
+        ls.append(labels[mask])
+        del feats, labels, counts, mask, tq
+    feats, labels = torch.cat(fs), torch.cat(ls)
+    del fs, ls
+    samples = len(labels)
+    if samples > 20_000_000:
+        pick = torch.randperm(samples, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))[:20_000_000]
+        feats, labels = feats[pick], labels[pick]
+    wts, hist = deg.train_stop_model(feats.contiguous(), labels.contiguous(), epochs=4, batch=8192)
+    del feats, labels
     log(f"[stop] trained on {samples} hops, loss {[round(h, 4) for h in hist]}")
     grid = [eps0] + [e for e in EPS_GRID if e > eps0][:7]
     points = []
@@ -368,6 +382,8 @@ def run_stop_sweep(args):
         if best is None or p["qps"] > best["qps"]:
             best = p
     line = {"stop_sweep": w.name, "n": w.n, "dim": w.dim, "queries": len(q), "k": K, "form": "float32, fixed entry",
+            "graph": "host-built file" if os.path.exists(graphs.graph_path(w)) else "device-built (batched Alg. 3-4)",
+            "graph_s": build_s, "train_queries": n_train,
             "target_recall": TARGET_RECALL, "plain": plain, "learned": best, "train_hops": samples,
             "loss": [round(h, 4) for h in hist], "points": points,
             "qps_ratio": best["qps"] / plain["qps"] if best else None,
@@ -546,6 +562,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the k = 1 / 100 and exploration points")
+    ap.add_argument("--train-queries", type=int, default=100_000, help="held-out queries traced for the stop network")
     ap.add_argument("--builder", default="host", choices=["host", "device"],
                     help="graph builder when the workload's graph file is missing")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")

@@ -107,6 +107,17 @@ DEG_API deg_status deg_build(const float* base_host, int64_t n, int32_t dim, con
 DEG_API deg_status deg_build_device(const float* base_host, int64_t n, int32_t dim, const deg_build_params* p,
                                     int32_t batch_div, volatile int64_t* progress, deg_index** out, void* stream);
 
+/* Grow an index by m vectors new_host [m][dim] float32 on the current GPU: they become vertices
+ * n .. n+m-1 and are inserted as deg_build_device inserts vertices (Sec. 5.2, Alg. 3 in batches of
+ * at most 1/batch_div of the graph, seeded at vertex 0; Alg. 4 for the new edges when p->i_opt >
+ * 0). The paper builds a graph by exactly such insertions; this makes the index grow after it is
+ * built. Copies the vectors. The host adjacency is replaced and the device copy released (upload
+ * again before searching); on an error the index is unchanged. p->degree must equal the index's.
+ * DEG_EINVAL on bad parameters (as deg_build_device), DEG_ECUDA on a device error, DEG_EGRAPH if
+ * the result violates a graph invariant. */
+DEG_API deg_status deg_insert_device(deg_index* idx, const float* new_host, int64_t m, const deg_build_params* p,
+                                     int32_t batch_div, void* stream);
+
 /* dynamicEdgeOptimization (Sec. 5.3, Alg. 5) on the current GPU over the index's graph:
  * p->refine_rounds rounds, each taking a random vertex v1 (SplitMix64 from p->seed) and running
  * optimizeEdge (Alg. 4; p->i_opt, p->k_opt, p->eps_opt) on each edge (v1, v2) that fails

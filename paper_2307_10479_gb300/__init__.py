@@ -68,6 +68,7 @@ def lib() -> ctypes.CDLL:
             "deg_build": (S, [P, i64, i32, ctypes.POINTER(BuildParams), P, ctypes.POINTER(P)]),
             "deg_build_device": (S, [P, i64, i32, ctypes.POINTER(BuildParams), i32, P, ctypes.POINTER(P), P]),
             "deg_refine_device": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
+            "deg_insert_device": (S, [P, P, i64, ctypes.POINTER(BuildParams), i32, P]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -164,6 +165,15 @@ class Index:
         _check(lib().deg_build_device(base.ctypes.data, base.shape[0], base.shape[1], ctypes.byref(p), batch_div, None,
                                       ctypes.byref(h), _stream_ptr(stream)))
         return cls(h)
+
+    def insert_device(self, vectors: np.ndarray, k_ext: int, eps_ext: float, k_opt: int = 0, eps_opt: float = 0.001,
+                      i_opt: int = 0, batch_div: int = 256, stream=None):
+        """Insert new vectors as vertices n .. n+m-1 (deg_insert_device); upload again afterwards."""
+        vectors = np.ascontiguousarray(vectors, np.float32)
+        _, _, degree = self.info()
+        p = BuildParams(degree, k_ext, eps_ext, k_opt or degree, eps_opt, i_opt, 0, 0)
+        _check(lib().deg_insert_device(self._h, vectors.ctypes.data, vectors.shape[0], ctypes.byref(p), batch_div,
+                                       _stream_ptr(stream)))
 
     def refine_device(self, rounds: int, k_opt: int, eps_opt: float, i_opt: int, seed: int = 0, stream=None) -> int:
         """Alg. 5 for `rounds` random vertices on the GPU (deg_refine_device); returns the improved count."""

@@ -982,20 +982,16 @@ int refine_graph_device(const float* x_host, const int32_t* adj_inout, int64_t n
     return B.download(adj_out, why);
 }
 
-int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,
-                       int32_t* adj_out, volatile int64_t* progress, deg_stream_t stream, std::string* why) {
-    const int32_t d = p.degree;
-    if (d > kMaxBuildDegree) return *why = "degree above 128", (int)cudaErrorInvalidValue;
-    if (p.k_ext > 1024 || p.k_opt > 1024) return *why = "k_ext and k_opt must be at most 1024", (int)cudaErrorInvalidValue;
-    if (p.i_opt > 6) return *why = "i_opt above 6", (int)cudaErrorInvalidValue;
-    if (batch_div < 1) return *why = "batch_div must be positive", (int)cudaErrorInvalidValue;
-    const int32_t kmax = std::min(1024, std::max({4 * p.k_ext, p.k_opt, d}));
-    DeviceBuilder B(n, dim, d, stream);
-    if (const int rc = B.init(x_host, nullptr, kmax, why)) return rc;
+namespace {
+
+// Inserts vertices first .. n-1 (Alg. 3, with Alg. 4 for the new edges when p.i_opt > 0) into the
+// graph on vertices 0 .. first-1, in batches of at most inserted / batch_div vertices.
+int extend_vertices(DeviceBuilder& B, const deg_build_params& p, int64_t first, int64_t n, int32_t batch_div,
+                    int32_t kmax, volatile int64_t* progress, std::string* why) {
     const bool optimise = p.i_opt > 0;
     std::vector<int32_t> ids, deferred;
     std::vector<std::vector<int32_t>> tasks;
-    int64_t next = d + 1, inserted = d + 1;
+    int64_t next = first, inserted = first;
     int32_t stalls = 0;
     while (next < n || !deferred.empty()) {
         int32_t ks = p.k_ext;
@@ -1029,9 +1025,39 @@ int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_bu
         }
         if (progress) *progress = inserted;
     }
+    return 0;
+}
+
+int check_build_params(const deg_build_params& p, int32_t batch_div, std::string* why) {
+    if (p.degree > kMaxBuildDegree) return *why = "degree above 128", (int)cudaErrorInvalidValue;
+    if (p.k_ext > 1024 || p.k_opt > 1024) return *why = "k_ext and k_opt must be at most 1024", (int)cudaErrorInvalidValue;
+    if (p.i_opt > 6) return *why = "i_opt above 6", (int)cudaErrorInvalidValue;
+    if (batch_div < 1) return *why = "batch_div must be positive", (int)cudaErrorInvalidValue;
+    return 0;
+}
+
+}  // namespace
+
+int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,
+                       int32_t* adj_out, volatile int64_t* progress, deg_stream_t stream, std::string* why) {
+    if (const int rc = check_build_params(p, batch_div, why)) return rc;
+    const int32_t kmax = std::min(1024, std::max({4 * p.k_ext, p.k_opt, p.degree}));
+    DeviceBuilder B(n, dim, p.degree, stream);
+    if (const int rc = B.init(x_host, nullptr, kmax, why)) return rc;
+    if (const int rc = extend_vertices(B, p, p.degree + 1, n, batch_div, kmax, progress, why)) return rc;
     if (p.refine_rounds > 0)
-        if (const int rc = refine_graph(B, n, d, p, why)) return rc;
+        if (const int rc = refine_graph(B, n, p.degree, p, why)) return rc;
     return B.download(adj_out, why);
+}
+
+int insert_vertices_device(const float* x_host, int32_t* adj, int64_t n_old, int64_t n, int32_t dim,
+                           const deg_build_params& p, int32_t batch_div, deg_stream_t stream, std::string* why) {
+    if (const int rc = check_build_params(p, batch_div, why)) return rc;
+    const int32_t kmax = std::min(1024, std::max({4 * p.k_ext, p.k_opt, p.degree}));
+    DeviceBuilder B(n, dim, p.degree, stream);
+    if (const int rc = B.init(x_host, adj, kmax, why)) return rc;
+    if (const int rc = extend_vertices(B, p, n_old, n, batch_div, kmax, nullptr, why)) return rc;
+    return B.download(adj, why);
 }
 
 }  // namespace deg

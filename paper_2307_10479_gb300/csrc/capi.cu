@@ -192,6 +192,38 @@ extern "C" deg_status deg_build_device(const float* base_host, int64_t n, int32_
     return DEG_OK;
 }
 
+extern "C" deg_status deg_insert_device(deg_index* idx, const float* new_host, int64_t m, const deg_build_params* p,
+                                        int32_t batch_div, void* stream) {
+    if (!idx || !p || (m > 0 && !new_host)) return fail(DEG_EINVAL, "deg_insert_device: NULL argument");
+    if (m < 0 || idx->n + m > INT32_MAX) return fail(DEG_EINVAL, "deg_insert_device: bad count");
+    if (p->degree != idx->degree || idx->degree > 128) return fail(DEG_EINVAL, "deg_insert_device: params.degree differs from the index's, or above 128");
+    if (p->k_ext < p->degree || p->k_ext > 1024 || p->i_opt < 0 || p->i_opt > 6 ||
+        (p->i_opt > 0 && (p->k_opt < 1 || p->k_opt > 1024)) || !(p->eps_ext >= 0.f) || !(p->eps_opt >= 0.f) || batch_div < 1)
+        return fail(DEG_EINVAL, "deg_insert_device: need degree <= k_ext <= 1024, 0 <= i_opt <= 6, 1 <= k_opt <= 1024, eps >= 0, batch_div >= 1");
+    if (m == 0) return DEG_OK;
+    const int64_t n_old = idx->n, n = n_old + m;
+    try {
+        idx->x.resize((size_t)n * idx->dim);
+        idx->adj.resize((size_t)n * idx->degree, -1);
+    } catch (const std::bad_alloc&) {
+        idx->x.resize((size_t)n_old * idx->dim);
+        idx->adj.resize((size_t)n_old * idx->degree);
+        return fail(DEG_ENOMEM, "deg_insert_device: host allocation failed");
+    }
+    std::memcpy(idx->x.data() + (size_t)n_old * idx->dim, new_host, sizeof(float) * (size_t)m * idx->dim);
+    std::string why;
+    const int e = insert_vertices_device(idx->x.data(), idx->adj.data(), n_old, n, idx->dim, *p, batch_div,
+                                         static_cast<deg_stream_t>(stream), &why);
+    if (e != 0) {
+        idx->x.resize((size_t)n_old * idx->dim);
+        idx->adj.resize((size_t)n_old * idx->degree);
+        return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "deg_insert_device: " + why);
+    }
+    idx->n = n;
+    free_device(idx);                                          // the device copy shows the old graph
+    return check_graph(idx->adj.data(), idx->n, idx->degree);
+}
+
 extern "C" deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream) {
     if (!idx || !p) return fail(DEG_EINVAL, "deg_refine_device: NULL argument");
     if (p->degree != idx->degree) return fail(DEG_EINVAL, "deg_refine_device: params.degree differs from the index's");

@@ -24,6 +24,10 @@ int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& 
 // [n][degree] written to adj_out (host). Returns a cudaError_t value (0 = success).
 int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,
                        int32_t* adj_out, volatile int64_t* progress, deg_stream_t stream, std::string* why);
+// Inserts vertices n_old .. n-1 (their rows in x_host [n][dim]) into the graph adj [n][degree] whose
+// first n_old rows hold a graph and the rest -1 (batched Alg. 3, Alg. 4 when p.i_opt > 0).
+int insert_vertices_device(const float* x_host, int32_t* adj, int64_t n_old, int64_t n, int32_t dim,
+                           const deg_build_params& p, int32_t batch_div, deg_stream_t stream, std::string* why);
 // Alg. 5 (p.refine_rounds rounds, p.i_opt / k_opt / eps_opt, SplitMix64(p.seed)) on the device over
 // an existing graph adj_in [n][degree]; the result goes to adj_out (may be adj_in).
 int refine_graph_device(const float* x_host, const int32_t* adj_in, int64_t n, int32_t dim, const deg_build_params& p,

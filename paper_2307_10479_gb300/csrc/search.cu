@@ -234,7 +234,8 @@ struct WarpState {
     float r2;
     int32_t hops, evals, peak;
     // for the learned stop's features
-    int32_t last_change, evals_change, hop_rins;
+    int32_t last_change, evals_change;   // hop and evaluation count of the last change of the top k of R
+    int32_t hop_rins;                    // insertions into R this hop
     float r2_first;
 };
 
@@ -565,8 +566,9 @@ __device__ bool admit_batch(WarpState& W, uint64_t key, bool take, const Radius&
 
 // Add a batch of result candidates (one per lane, where `take`) to R, sorted ascending: merge,
 // keep the ks smallest. The same R, radius and trim as one-by-one insertion (Alg. 1 admits them
-// all against the radius from before the hop).
-__device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int lane) {
+// all against the radius from before the hop). For the learned stop, a key landing among the
+// first k (the results returned) marks this hop as the last change of the top k.
+__device__ void result_batch(WarpState& W, int ks, int k, uint64_t key, bool take, int lane) {
     const unsigned mr = __ballot_sync(0xffffffffu, take);
     if (!mr) return;
     const int m = __popc(mr), rn = W.res_n;
@@ -598,12 +600,13 @@ __device__ void result_batch(WarpState& W, int ks, uint64_t key, bool take, int 
     }
     if (knew >= 0 && knew < ks) W.res[knew] = key;
     const int added = __popc(__ballot_sync(0xffffffffu, knew >= 0 && knew < ks));
+    const bool top = __any_sync(0xffffffffu, knew >= 0 && knew < k);
     W.res_n = min(rn + m, ks);
     __syncwarp();
-    if (added) {
+    W.hop_rins += added;
+    if (top) {
         W.last_change = W.hops;
         W.evals_change = W.evals;
-        W.hop_rins += added;
     }
     if (rn + m > ks) {                                        // R overflowed k: r = max R
         if (!W.trimmed) W.r2_first = key_d2(W.res[ks - 1]);
@@ -738,7 +741,7 @@ __device__ void finish_query(const Params& P, WarpState& W, int q, const float* 
         P.dists[(int64_t)q * P.k + i] = ok ? sqrtf(key_d2(v)) : __int_as_float(0x7f800000);
     }
     if (P.rec_feats) {
-        // label of the hop recorded in slot t (hop t+1): 1 if R never changed after that hop
+        // label of the hop recorded in slot t (hop t+1): 1 if the top k of R never changed after it
         const int rec = min(W.hops, P.rec_cap);
         for (int t = lane; t < rec; t += 32) P.rec_labels[(int64_t)q * P.rec_cap + t] = (t + 1 >= W.last_change) ? 1 : 0;
         if (lane == 0) P.rec_counts[q] = rec;
@@ -907,7 +910,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             const int i = i0 + lane;
             const bool valid = i < cnt;
             const float d2 = valid ? W.cd2[i] : inf;
-            result_batch(W, P.ks, make_key(d2, valid ? W.ccid[i] : -1), valid && d2 <= r2pre, lane);
+            result_batch(W, P.ks, P.k, make_key(d2, valid ? W.ccid[i] : -1), valid && d2 <= r2pre, lane);
         }
         // 5. S <- S u {n : d(n) <= r (1 + eps)} against the radius after the hop: a candidate outside
         //    it could only ever be popped to fail the stop test (r never grows), and the next key
@@ -927,8 +930,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         W.peak = max(W.peak, W.fn + W.back_n);
         __syncwarp();
-        // the learned stop is asked every fourth hop, and only once R has not changed for two hops
-        // (while R still changes, more expansion is evidently still paying)
+        // the learned stop is asked every fourth hop, and only once the top k of R have not changed
+        // for two hops (while they still change, more expansion is evidently still paying)
         const bool ask = P.learned && (W.hops & 3) == 0 && W.hops - W.last_change >= 2;
         if (ask || P.rec_feats) {
             float x[kStopFeatures];

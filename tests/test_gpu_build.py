@@ -110,3 +110,27 @@ def test_smallest_graphs_and_bad_arguments():
             deg.Index.build_device(synth.uniform(200, 4, 3), eps_ext=0.2, **kw)
     with pytest.raises(deg.DegError):
         deg.Index.build_device(base, 8, 8, 0.2, batch_div=0)
+
+
+def test_insert_grows_a_graph_like_a_build():
+    # a graph over the first 6,000 rows, then the last 2,000 inserted by deg_insert_device: the
+    # invariants hold over all 8,000, and Alg. 1 finds the new vertices as well as the old
+    import paper_2307_10479_gb300 as deg
+    w = synth.scaled(synth.WORKLOADS["sift-1m-d128"], 8_000, 200)
+    base, q = w.base(), w.queries()
+    idx = deg.Index.build_device(base[:6000], 30, 60, 0.2, k_opt=30, i_opt=5)
+    idx.insert_device(base[6000:], 60, 0.2, k_opt=30, i_opt=5)
+    n, dim, degree = idx.info()
+    adj = idx.adjacency()
+    assert (n, degree) == (8000, 30) and oracle.check_graph(adj) == 0
+    full = deg.Index.build_device(base, 30, 60, 0.2, k_opt=30, i_opt=5).adjacency()
+    gt, _ = oracle.knn_bruteforce(base, q, 10)
+    entry = np.full(len(q), oracle.median_vertex(base), np.int32)
+    r_ins = recall(oracle.range_search(base, adj, q, entry, 10, 0.1)[0], gt)
+    r_full = recall(oracle.range_search(base, full, q, entry, 10, 0.1)[0], gt)
+    assert r_ins >= r_full - 0.02, (r_ins, r_full)
+    idx.upload()
+    ids, _ = idx.search(torch.from_numpy(base[6000:6100]).cuda(), k=1, eps=0.1)
+    assert np.mean(ids.cpu().numpy()[:, 0] == np.arange(6000, 6100)) >= 0.99   # new rows find themselves
+    with pytest.raises(deg.DegError):
+        idx.insert_device(base[:10], 4, 0.2)                 # k_ext below the degree

@@ -25,7 +25,8 @@ def build(w: synth.Workload, base, builder: str = "host") -> Index:
     "device" (batched, on the current GPU)."""
     t0 = time.time()
     if builder == "device":
-        idx = Index.build_device(base, w.degree, w.k_ext, w.eps_ext, k_opt=w.k_opt, eps_opt=w.eps_opt, i_opt=w.i_opt)
+        idx = Index.build_device(base, w.degree, w.k_ext, w.eps_ext, k_opt=w.k_opt, eps_opt=w.eps_opt, i_opt=w.i_opt,
+                                 batch_div=64)
     else:
         idx = Index.build(base, w.degree, w.k_ext, w.eps_ext, w.k_opt, w.eps_opt, w.i_opt)
     print(f"[graphs] built {w.name} ({w.n} x {w.dim}, d={w.degree}) with the {builder} builder in "

@@ -157,6 +157,17 @@ DEG_API deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* stre
  * (E4M3 codes) and scales_host [n] float32. DEG_ENOTREADY if that copy was not uploaded. */
 DEG_API deg_status deg_export_codes(const deg_index* idx, int32_t precision, void* codes_host, float* scales_host);
 
+/* Learned entry points (not in the paper): a second set of routing pivots (entry_mode 2) of k
+ * vertices learned from the data; the sampled pivots (entry_mode 1) stay. Lloyd's algorithm (k-means) runs `iters` rounds on the device
+ * from k rows spaced evenly through the stored order (every row to its nearest centroid, every
+ * centroid to the mean of its rows; an empty cluster keeps its centroid); each centroid is then
+ * replaced by the base vertex nearest to it, and those vertices are the learned pivots, used by
+ * the batch routing and the serving loop alike. Training again replaces them. sizes_host (nullable) [k] gets the final cluster
+ * sizes. Needs an uploaded index and a dimension divisible by 4. Synchronises `stream`.
+ * DEG_EINVAL when k is outside 1 ... min(4096, n) or iters outside 0 ... 1000; DEG_ENOTREADY
+ * before deg_upload; DEG_ECUDA on a device error. */
+DEG_API deg_status deg_train_entry(deg_index* idx, int32_t k, int32_t iters, int64_t* sizes_host, void* stream);
+
 /* The entry vertex computed by deg_upload, or -1 before it. */
 DEG_API int32_t deg_entry_vertex(const deg_index* idx);
 
@@ -181,7 +192,9 @@ typedef struct {
                              finished by a second kernel with room for all n vertices          */
     int32_t entry_mode;   /* plain searches with no seeds: 0 = the fixed entry vertex (paper,
                              Sec. 5.4); 1 = per query, the nearest of the index's pivot vertices
-                             (about n/256, at most 4096, chosen at upload) -- not in the paper */
+                             (about n/256, at most 4096, chosen at upload); 2 = the nearest of
+                             the learned entry points (deg_train_entry) -- 1 and 2 are not in
+                             the paper */
     int32_t learned_stop; /* 1: every fourth hop, once R has not changed for two hops, the
                              index's stop network (deg_set_stop_model) may end the search
                              early; the eps test still applies. Not in the paper; 0 = the
@@ -279,7 +292,8 @@ typedef struct {
     int32_t kmax;            /* largest k of any request, 1..1024                                 */
     int32_t precision;       /* DEG_F32 | DEG_BF16 | DEG_FP8 (uploaded)                           */
     int32_t rerank;          /* reduced precision: re-rank width (0 = k)                          */
-    int32_t entry_mode;      /* vector requests: 0 fixed entry vertex, 1 nearest pivot            */
+    int32_t entry_mode;      /* vector requests: 0 fixed entry vertex, 1 nearest pivot, 2 nearest
+                                learned entry point                                               */
     int32_t learned_stop;    /* 1: use the index's stop network                                    */
     double idle_timeout_s;   /* end the kernel when no request arrives for this long (> 0)         */
 } deg_serve_config;

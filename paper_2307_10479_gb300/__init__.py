@@ -25,6 +25,9 @@ _lock = threading.Lock()
 _lib = None
 
 
+ENTRY_MODES = {"fixed": 0, "pivot": 1, "learned": 2}
+
+
 class DegError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"[deg status {status}] {msg}")
@@ -76,6 +79,7 @@ def lib() -> ctypes.CDLL:
             "deg_get_adjacency": (S, [P, P]),
             "deg_upload": (S, [P, i32, P]),
             "deg_entry_vertex": (i32, [P]),
+            "deg_train_entry": (S, [P, i32, i32, P, P]),
             "deg_export_codes": (S, [P, i32, P, P]),
             "deg_free": (None, [P]),
             "deg_search": (S, [P, P, i64, i32, f32, P, P, P, P, P]),
@@ -232,6 +236,13 @@ class Index:
         _check(lib().deg_export_codes(self._h, DEG_FP8, codes.ctypes.data, scales.ctypes.data))
         return codes, scales
 
+    def train_entry(self, k: int = 4096, iters: int = 10, stream=None) -> np.ndarray:
+        """Learned entry points: k-means on the device, pivots = vertices nearest the centroids
+        (deg_train_entry). Returns the cluster sizes."""
+        sizes = np.empty(k, np.int64)
+        _check(lib().deg_train_entry(self._h, k, iters, sizes.ctypes.data, _stream_ptr(stream)))
+        return sizes
+
     @property
     def entry_vertex(self) -> int:
         return int(lib().deg_entry_vertex(self._h))
@@ -259,7 +270,7 @@ class Index:
         status = torch.empty(nq, dtype=torch.int32, device=dev) if with_status else None
         trace = torch.empty((nq, 4), dtype=torch.int32, device=dev) if with_trace else None
         p = SearchParams(k, eps, PRECISIONS[precision], rerank, max_hops, visited_cap, queue_cap,
-                         {"fixed": 0, "pivot": 1}[entry], 1 if learned_stop else 0)
+                         ENTRY_MODES[entry], 1 if learned_stop else 0)
         _check(lib().deg_search_ex(self._h, ctypes.byref(p), None if explore else _dptr(queries), _dptr(seeds),
                                    1 if explore else 0, nq, _dptr(ids), _dptr(dists), _dptr(status), _dptr(trace),
                                    _stream_ptr(stream)))
@@ -282,7 +293,7 @@ class Index:
         explore = explore_ids is not None
         nq = explore_ids.shape[0] if explore else queries.shape[0]
         ids, dists = out if out is not None else (np.empty((nq, k), np.int32), np.empty((nq, k), np.float32))
-        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry],
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, ENTRY_MODES[entry],
                          1 if learned_stop else 0)
         qptr = None if explore else ctypes.c_void_p(queries.ctypes.data)
         sptr = ctypes.c_void_p(explore_ids.ctypes.data) if explore else None
@@ -302,7 +313,7 @@ class Index:
         feats = torch.zeros((nq, cap, STOP_FEATURES), dtype=torch.float32, device=queries.device)
         labels = torch.zeros((nq, cap), dtype=torch.int32, device=queries.device)
         counts = torch.zeros(nq, dtype=torch.int32, device=queries.device)
-        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, {"fixed": 0, "pivot": 1}[entry], 0)
+        p = SearchParams(k, eps, PRECISIONS[precision], rerank, 0, 0, 0, ENTRY_MODES[entry], 0)
         _check(lib().deg_stop_record(self._h, ctypes.byref(p), _dptr(queries), nq, cap, _dptr(feats), _dptr(labels),
                                      _dptr(counts), _stream_ptr(stream)))
         return feats, labels, counts
@@ -321,7 +332,7 @@ class Server:
         self.index = index
         self.kmax = kmax
         self.dim = index.info()[1]
-        cfg = ServeConfig(capacity, kmax, PRECISIONS[precision], rerank, {"fixed": 0, "pivot": 1}[entry],
+        cfg = ServeConfig(capacity, kmax, PRECISIONS[precision], rerank, ENTRY_MODES[entry],
                           1 if learned_stop else 0, float(idle_timeout_s))
         self._h = ctypes.c_void_p()
         _check(lib().deg_serve_start(index._h, ctypes.byref(cfg), ctypes.byref(self._h)))

@@ -96,6 +96,9 @@ void free_device(deg_index* idx) {
     cudaFree(d.pivots);
     knn_plan_destroy(d.route_plan);
     d.route_plan = nullptr;
+    knn_plan_destroy(d.lroute_plan);
+    d.lroute_plan = nullptr;
+    cudaFree(d.lpivots);
     cudaFree(d.stop_w);
     d = DeviceIndex{};
     workspace_free(idx->ws);
@@ -396,6 +399,17 @@ extern "C" deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* s
 
 extern "C" int32_t deg_entry_vertex(const deg_index* idx) { return idx ? idx->dev.entry : -1; }
 
+extern "C" deg_status deg_train_entry(deg_index* idx, int32_t k, int32_t iters, int64_t* sizes_host, void* stream) {
+    if (!idx) return fail(DEG_EINVAL, "deg_train_entry: NULL index");
+    if (!idx->dev.x32) return fail(DEG_ENOTREADY, "deg_train_entry: upload the index first");
+    if (k < 1 || k > 4096 || k > idx->n || iters < 0 || iters > 1000)
+        return fail(DEG_EINVAL, "deg_train_entry: need 1 <= k <= min(4096, n), 0 <= iters <= 1000");
+    std::string why;
+    const int e = train_entry_points(idx->dev, k, iters, static_cast<deg_stream_t>(stream), sizes_host, &why);
+    if (e != 0) return fail(e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, "deg_train_entry: " + why);
+    return DEG_OK;
+}
+
 extern "C" deg_status deg_export_codes(const deg_index* idx, int32_t precision, void* codes_host, float* scales_host) {
     if (!idx || !codes_host) return fail(DEG_EINVAL, "deg_export_codes: NULL argument");
     const DeviceIndex& d = idx->dev;
@@ -453,9 +467,10 @@ deg_status validate_search(const deg_index* idx, const deg_search_params* p, con
     if (p->max_hops < 0) return fail(DEG_EINVAL, "search: max_hops must be >= 0");
     if (p->visited_cap != 0) return fail(DEG_EINVAL, "search: visited_cap is reserved and must be 0");
     if (p->queue_cap < 0 || p->queue_cap > 32768) return fail(DEG_EINVAL, "search: queue_cap must be in [0, 32768]");
-    if (p->entry_mode != 0 && p->entry_mode != 1) return fail(DEG_EINVAL, "search: entry_mode must be 0 or 1");
+    if (p->entry_mode < 0 || p->entry_mode > 2) return fail(DEG_EINVAL, "search: entry_mode must be 0, 1 or 2");
+    if (p->entry_mode == 2 && !idx->dev.lpivots) return fail(DEG_ENOTREADY, "search: no learned entry points (deg_train_entry)");
     if (p->learned_stop != 0 && p->learned_stop != 1) return fail(DEG_EINVAL, "search: learned_stop must be 0 or 1");
-    if (p->entry_mode == 1 && (explore || seeds)) return fail(DEG_EINVAL, "search: entry_mode 1 needs query vectors and no seeds");
+    if (p->entry_mode >= 1 && (explore || seeds)) return fail(DEG_EINVAL, "search: entry_mode 1 or 2 needs query vectors and no seeds");
     if (explore ? (queries != nullptr || seeds == nullptr) : (queries == nullptr && nq > 0))
         return fail(DEG_EINVAL, "search: explore needs vertex ids and no query vectors; search needs vectors");
     return DEG_OK;
@@ -736,7 +751,7 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
         return fail(DEG_EINVAL, "serve_start: need capacity >= 1, 1 <= kmax <= 1024, idle_timeout_s > 0");
     if (cfg->precision < DEG_F32 || cfg->precision > DEG_FP8 || !(idx->uploaded_mask & (1 << cfg->precision)))
         return fail(DEG_ENOTREADY, "serve_start: precision copy not uploaded");
-    if (cfg->entry_mode != 0 && cfg->entry_mode != 1) return fail(DEG_EINVAL, "serve_start: entry_mode must be 0 or 1");
+    if (cfg->entry_mode < 0 || cfg->entry_mode > 2) return fail(DEG_EINVAL, "serve_start: entry_mode must be 0, 1 or 2");
     if (cfg->learned_stop && !idx->dev.stop_w) return fail(DEG_ENOTREADY, "serve_start: no stop model");
     if (cfg->rerank < 0 || cfg->rerank > 1024) return fail(DEG_EINVAL, "serve_start: rerank out of range");
     std::string why;

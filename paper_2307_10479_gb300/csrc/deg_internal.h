@@ -61,6 +61,11 @@ struct DeviceIndex {
     int32_t npivots = 0;
     struct KnnPlan* route_plan = nullptr;   // nearest-pivot search over the pivots' rows (knn_tc.cu)
     float far_tau = 3.4e38f;      // routed queries farther than this from their pivot start first
+    // learned entry points (deg_train_entry): the same routing over trained pivots (entry_mode 2)
+    int32_t* lpivots = nullptr;
+    int32_t lnpivots = 0;
+    struct KnnPlan* lroute_plan = nullptr;
+    float lfar_tau = 3.4e38f;
     uint16_t* stop_w = nullptr;   // learned-stop weights, bfloat16, inference layout (mlp.cu)
     float stop_logit = 0.f;       // stop when logit(stop) - logit(continue) > this
 };
@@ -147,11 +152,17 @@ int compute_entry_vertex(DeviceIndex& ix, deg_stream_t stream, std::string* why)
 // Reorder rows and adjacency by nearest pivot (layout.cu); fills old2new/new2old. Synchronous.
 int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why);
 
+// Learned entry points (layout.cu): k-means (Lloyd, iters rounds) over the rows, each centroid
+// replaced by its nearest row; those rows become the routing pivots. sizes_out (nullable, host,
+// [k]) gets each final cluster's size. Synchronous.
+int train_entry_points(DeviceIndex& ix, int32_t k, int32_t iters, deg_stream_t stream, int64_t* sizes_out,
+                       std::string* why);
+
 // Entry routing (layout.cu): seeds[q] = internal id of the pivot nearest to query q, dists[q] its
 // distance; if order is given, a work order with the queries farther than far_tau from their
 // pivot first (cursors: two int32 of device scratch).
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    float* dists, int32_t* order, int32_t* cursors, deg_stream_t stream, std::string* why);
+                    float* dists, int32_t* order, int32_t* cursors, bool learned, deg_stream_t stream, std::string* why);
 
 // Reduced-precision copies (quantize.cu).
 int make_bf16_copy(DeviceIndex& ix, deg_stream_t stream, std::string* why);

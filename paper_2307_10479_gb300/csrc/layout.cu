@@ -267,21 +267,158 @@ int apply_locality_layout(DeviceIndex& ix, deg_stream_t stream, std::string* why
 namespace deg {
 
 int route_to_pivots(const DeviceIndex& ix, const float* queries, int64_t nq, int32_t* labels, int32_t* seeds,
-                    float* dists, int32_t* order, int32_t* cursors, deg_stream_t stream, std::string* why) {
+                    float* dists, int32_t* order, int32_t* cursors, bool learned, deg_stream_t stream, std::string* why) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (!ix.route_plan) return *why = "no routing plan (upload the index first)", (int)cudaErrorInvalidValue;
+    KnnPlan* plan = learned ? ix.lroute_plan : ix.route_plan;
+    const int32_t* pivots = learned ? ix.lpivots : ix.pivots;
+    const float tau = learned ? ix.lfar_tau : ix.far_tau;
+    if (!plan) return *why = learned ? "no learned entry points (deg_train_entry)" : "no routing plan (upload the index first)",
+                      (int)cudaErrorInvalidValue;
     if (nq <= 0) return 0;
     // exact float32 nearest pivot (ties to the lower pivot index), tensor-core filtered
-    if (const int r = knn_plan_run(ix.route_plan, queries, nq, labels, dists, stream, why)) return r;
+    if (const int r = knn_plan_run(plan, queries, nq, labels, dists, stream, why)) return r;
     if (order) {
         cudaMemsetAsync(cursors, 0, 2 * sizeof(int32_t), st);
-        route_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, dists, (int32_t)nq, ix.pivots, ix.far_tau,
-                                                                     seeds, order, cursors);
+        route_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, dists, (int32_t)nq, pivots, tau, seeds,
+                                                                     order, cursors);
     } else {
-        map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, ix.pivots, seeds);
+        map_ids_kernel<<<(unsigned)((nq + 255) / 256), 256, 0, st>>>(labels, (int32_t)nq, pivots, seeds);
     }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
+    return 0;
+}
+
+}  // namespace deg
+
+// ---- learned entry points (not in the paper) --------------------------------------------------
+// The pivot routing starts each query at the pivot nearest to it. Here a second set of pivots is
+// learned from the data instead of sampled: K centroids trained by Lloyd's algorithm (k-means:
+// assign every row to its nearest centroid, move every centroid to the mean of its rows, repeat),
+// each replaced by the base vertex nearest to it. With entry_mode 2 a query starts at the nearest
+// of those vertices, found exactly as with the sampled pivots (entry_mode 1).
+namespace deg {
+namespace {
+
+// sums[label][c] += row[c], counts[label] += 1 (one warp per row)
+__global__ void centroid_sums_kernel(const float* __restrict__ x, int64_t n, int32_t dim, int32_t dim_pad,
+                                     const int32_t* __restrict__ labels, float* __restrict__ sums, int32_t* __restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n;
+         v += (int64_t)gridDim.x * (blockDim.x >> 5)) {
+        const int32_t l = labels[v];
+        for (int c = lane; c < dim; c += 32) atomicAdd(sums + (int64_t)l * dim_pad + c, x[v * dim_pad + c]);
+        if (lane == 0) atomicAdd(counts + l, 1);
+    }
+}
+
+// centroid = sums / count; an empty cluster keeps its centroid
+__global__ void centroid_update_kernel(float* __restrict__ cent, const float* __restrict__ sums,
+                                       const int32_t* __restrict__ counts, int32_t k, int32_t dim, int32_t dim_pad) {
+    const int64_t total = (int64_t)k * dim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = i / dim;
+        const int d = (int)(i - c * dim);
+        if (counts[c] > 0) cent[c * dim_pad + d] = sums[c * dim_pad + d] / (float)counts[c];
+    }
+}
+
+// contiguous [k][dim] copy of [k][dim_pad] rows (the k-NN calls take row-major rows dim floats apart)
+__global__ void compact_rows_kernel(const float* __restrict__ in, int32_t k, int32_t dim, int32_t dim_pad, float* __restrict__ out) {
+    const int64_t total = (int64_t)k * dim;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[(i / dim) * dim_pad + i % dim];
+}
+
+}  // namespace
+
+int train_entry_points(DeviceIndex& ix, int32_t k, int32_t iters, deg_stream_t stream, int64_t* sizes_out,
+                       std::string* why) {
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t n = ix.n;
+    if (k < 1 || k > 4096 || k > n) return *why = "k must be in 1 ... min(4096, n)", (int)cudaErrorInvalidValue;
+    if (ix.dim % 4 != 0) return *why = "learned entry points need a dimension divisible by 4", (int)cudaErrorInvalidValue;
+    float *cent = nullptr, *sums = nullptr, *d2 = nullptr, *cdist = nullptr, *cflat = nullptr;
+    int32_t *labels = nullptr, *counts = nullptr, *iota = nullptr, *med = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(cent); cudaFree(sums); cudaFree(d2); cudaFree(cdist); cudaFree(cflat);
+        cudaFree(labels); cudaFree(counts); cudaFree(iota); cudaFree(med);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&cent, sizeof(float) * k * ix.dim_pad)) != cudaSuccess ||
+        (e = cudaMalloc(&sums, sizeof(float) * k * ix.dim_pad)) != cudaSuccess ||
+        (e = cudaMalloc(&cflat, sizeof(float) * k * ix.dim)) != cudaSuccess ||
+        (e = cudaMalloc(&d2, sizeof(float) * n)) != cudaSuccess || (e = cudaMalloc(&cdist, sizeof(float) * k)) != cudaSuccess ||
+        (e = cudaMalloc(&labels, sizeof(int32_t) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&counts, sizeof(int32_t) * k)) != cudaSuccess ||
+        (e = cudaMalloc(&iota, sizeof(int32_t) * k)) != cudaSuccess || (e = cudaMalloc(&med, sizeof(int32_t) * k)) != cudaSuccess) {
+        cleanup();
+        return *why = std::string("entry training buffers: ") + cudaGetErrorString(e), (int)e;
+    }
+    // start: k rows evenly spaced through the (layout-ordered) rows
+    pivot_ids_kernel<<<(k + 255) / 256, 256, 0, st>>>(med, k, n / k);
+    pivot_ids_kernel<<<(k + 255) / 256, 256, 0, st>>>(iota, k, 1);
+    {
+        // gather the start rows: cent[c] = x32[med[c]]
+        std::vector<int32_t> h(k);
+        if ((e = cudaMemcpyAsync(h.data(), med, sizeof(int32_t) * k, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+            cleanup();
+            return *why = cudaGetErrorString(e), (int)e;
+        }
+        for (int32_t c = 0; c < k && e == cudaSuccess; ++c)
+            e = cudaMemcpyAsync(cent + (int64_t)c * ix.dim_pad, ix.x32 + (int64_t)h[c] * ix.dim_pad,
+                                sizeof(float) * ix.dim_pad, cudaMemcpyDeviceToDevice, st);
+    }
+    for (int32_t it = 0; it <= iters && e == cudaSuccess; ++it) {
+        nearest_pivot_kernel<<<(unsigned)((n + kTile - 1) / kTile), 256, 0, st>>>(ix.x32, ix.dim_pad, cent, n, ix.dim,
+                                                                                  ix.dim_pad, iota, k, labels, d2);
+        if (it == iters) break;                           // the last assignment is the final one
+        cudaMemsetAsync(sums, 0, sizeof(float) * k * ix.dim_pad, st);
+        cudaMemsetAsync(counts, 0, sizeof(int32_t) * k, st);
+        centroid_sums_kernel<<<2048, 256, 0, st>>>(ix.x32, n, ix.dim, ix.dim_pad, labels, sums, counts);
+        centroid_update_kernel<<<512, 256, 0, st>>>(cent, sums, counts, k, ix.dim, ix.dim_pad);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        cleanup();
+        return *why = std::string("entry training: ") + cudaGetErrorString(e), (int)e;
+    }
+    // the vertex nearest to each centroid (exact k-NN over all rows, internal ids)
+    compact_rows_kernel<<<256, 256, 0, st>>>(cent, k, ix.dim, ix.dim_pad, cflat);
+    if (const int r = launch_knn_exact(ix.x32, n, cflat, k, ix.dim, 1, med, cdist, stream, why)) {
+        cleanup();
+        return r;
+    }
+    // routing over the new pivots' rows; the work order's threshold from the rows' centroid distances
+    KnnPlan* plan = nullptr;
+    if (const int r = knn_plan_create(&plan, ix.x32, ix.dim_pad, med, k, ix.dim, 1, 256, stream, why)) {
+        cleanup();
+        return r;
+    }
+    std::vector<float> h((size_t)n);
+    std::vector<int32_t> hl(sizes_out ? (size_t)n : 0);
+    if ((e = cudaMemcpy(h.data(), d2, sizeof(float) * n, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+        (sizes_out && (e = cudaMemcpy(hl.data(), labels, sizeof(int32_t) * n, cudaMemcpyDeviceToHost)) != cudaSuccess)) {
+        knn_plan_destroy(plan);
+        cleanup();
+        return *why = cudaGetErrorString(e), (int)e;
+    }
+    if (sizes_out) {
+        for (int32_t c = 0; c < k; ++c) sizes_out[c] = 0;
+        for (int64_t v = 0; v < n; ++v) ++sizes_out[hl[v]];
+    }
+    const size_t r = (size_t)std::min<int64_t>(n - 1, n - std::max<int64_t>(1, n / 32));
+    std::nth_element(h.begin(), h.begin() + r, h.end());
+    knn_plan_destroy(ix.lroute_plan);
+    ix.lroute_plan = plan;
+    cudaFree(ix.lpivots);
+    ix.lpivots = med;
+    med = nullptr;
+    ix.lnpivots = k;
+    ix.lfar_tau = std::sqrt(std::max(h[r], 0.f));
+    cleanup();
     return 0;
 }
 

@@ -53,7 +53,13 @@ constexpr int kWarpsPerBlock = 4;
 constexpr int kBlocksPerSM = DEG_SEARCH_BLOCKS_PER_SM;   // occupancy target: 24 warps per SM (85 registers)
 constexpr uint64_t kEmptyKey = ~0ull;
 constexpr int kMaxDegree = 128;
-constexpr int kFront = 128;              // sorted on-chip part of S
+#ifndef DEG_SEARCH_FRONT
+#define DEG_SEARCH_FRONT 128
+#endif
+#ifndef DEG_SEARCH_ROW_PREFETCH_BYTES
+#define DEG_SEARCH_ROW_PREFETCH_BYTES 256
+#endif
+constexpr int kFront = DEG_SEARCH_FRONT;  // sorted on-chip part of S (a power of two, >= 32)
 constexpr int kBackPool = 32768;         // device-memory part of S in the main kernel
 constexpr int kTouchCap = 8192;          // visited ids recorded per query for clearing C afterwards
 
@@ -876,7 +882,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             const int j = j0 + lane;
             const int2 e = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : make_int2(-1, -1);
             const int32_t nb = e.x;
-            if (nb >= 0 && P.row_bytes <= 256) {
+            if (nb >= 0 && P.row_bytes <= DEG_SEARCH_ROW_PREFETCH_BYTES) {
                 // start pulling the row into L2 while the visited test is in flight (a visited
                 // neighbour's row is usually there already); float32 rows (four lines) lose by it
                 const uint8_t* row = P.rows + (int64_t)nb * P.row_bytes;
@@ -1139,7 +1145,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
             Q.explore = 0;
             Q.queries = S.vecs + (int64_t)r * P.dim;
             Q.seeds = nullptr;
-            if (S.entry_mode == 1) {
+            if (S.entry_mode >= 1) {
                 for (int d = lane; d < dim4; d += 32) qv[d] = d < P.dim ? Q.queries[d] : 0.f;
                 __syncwarp();
                 const int32_t sd = route_one(P, pivots, np, qv, lane);
@@ -1339,11 +1345,11 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
     P.seeds = a.seeds;
     P.seeds2 = a.seeds2;
     P.explore = a.explore;
-    if (a.entry_mode == 1 && !a.explore && !a.seeds) {
+    if (a.entry_mode >= 1 && !a.explore && !a.seeds) {
         // route every query to its nearest pivot first; those become internal seeds
         const int e = route_to_pivots(ix, a.queries, a.nq, ws.route, ws.route + ws.cap_q,
                                       reinterpret_cast<float*>(ws.route + 2 * ws.cap_q), ws.route + 3 * ws.cap_q,
-                                      ws.route + 4 * ws.cap_q, stream, why);
+                                      ws.route + 4 * ws.cap_q, a.entry_mode == 2, stream, why);
         if (e != 0) return e;
         P.seeds = ws.route + ws.cap_q;
         P.order = ws.route + 3 * ws.cap_q;
@@ -1439,25 +1445,28 @@ int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* 
     P.slots = ws.slots;
     P.bstride = ws.bcap;
     P.bcap = ws.bcap;
+    const int32_t* piv = a.entry_mode == 2 ? ix.lpivots : ix.pivots;
+    const int32_t npiv = a.entry_mode == 2 ? ix.lnpivots : ix.npivots;
+    if (a.entry_mode == 2 && !piv) return *why = "no learned entry points (deg_train_entry)", (int)cudaErrorInvalidValue;
     ServeRing S{a.vecs, reinterpret_cast<const int4*>(a.meta), a.ids, a.dists, a.status, a.trace, a.done, a.tail,
                 a.stop, a.kstatus, a.claim, a.cap, a.kmax, a.entry_mode, a.idle_ns};
     if (a.precision == DEG_F32) {
         P.rows = reinterpret_cast<const uint8_t*>(ix.x32);
         P.row_bytes = 4ll * ix.dim_pad;
         P.nchunk = ix.dim_pad / 4;
-        return dispatch_serve<F32Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
+        return dispatch_serve<F32Rows>(P, S, piv, npiv, st, warps, why);
     }
     if (a.precision == DEG_BF16) {
         P.rows = reinterpret_cast<const uint8_t*>(ix.xbf);
         P.row_bytes = 2ll * ix.dim_pad16;
         P.nchunk = ix.dim_pad16 / 8;
-        return dispatch_serve<BF16Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
+        return dispatch_serve<BF16Rows>(P, S, piv, npiv, st, warps, why);
     }
     P.rows = ix.x8;
     P.row_bytes = ix.dim_pad8;
     P.nchunk = ix.dim_pad8 / 16;
     P.norm8 = reinterpret_cast<const float2*>(ix.norm8);
-    return dispatch_serve<FP8Rows>(P, S, ix.pivots, ix.npivots, st, warps, why);
+    return dispatch_serve<FP8Rows>(P, S, piv, npiv, st, warps, why);
 }
 
 }  // namespace deg

@@ -659,9 +659,19 @@ def main():
     forms["plain float32, fixed entry"] = plain
     for name in list(FORMS)[1:]:
         forms[name], _ = measure(name, FORMS[name], max(3, args.steps // 4), args.warmup)
+    # learned entry points: k-means on the device (as many as the sampled pivots, 10 rounds), each
+    # centroid replaced by its nearest vertex; then the pivot forms again from those entries
+    t_e = time.time()
+    sizes = idx.train_entry(len(idx.pivots()), 10)
+    entry_train_s = time.time() - t_e
+    log(f"[bench] learned entry: {len(sizes)} points in {entry_train_s:.1f} s (cluster sizes {sizes.min()}-{sizes.max()})")
+    for name in [nm for nm in list(FORMS) if "pivot entry" in nm]:
+        lname = name.replace("pivot entry", "learned entry")
+        FORMS[lname] = dict(FORMS[name], entry="learned")
+        forms[lname], _ = measure(lname, FORMS[lname], max(3, args.steps // 4), args.warmup)
     # learned early stop: trained (untimed) with the library's kernels on traces of 50,000 held-out
-    # queries of the fp8 / pivot-entry form, then measured like the other forms
-    base_name = f"fp8 + re-rank {args.rerank}, pivot entry"
+    # queries of the faster fp8 form (sampled or learned entry), then measured like the other forms
+    base_name = max((nm for nm in forms if nm.startswith("fp8")), key=lambda nm: forms[nm]["qps"])
     t_eps = forms[base_name]["eps"] + 0.01
     tq = torch.from_numpy(w.training_queries(50000)).cuda()
     feats, labels, counts = idx.stop_record(tq, k=K, eps=t_eps, cap=512, **FORMS[base_name])
@@ -762,11 +772,13 @@ def main():
         "knn_exact": knn_line(knn_ms, len(q), n, dim),
         "precision": precision,
         "other_points": extra,
+        "learned_entry": {"points": int(len(sizes)), "kmeans_rounds": 10, "train_s": entry_train_s,
+                          "cluster_size_min": int(sizes.min()), "cluster_size_max": int(sizes.max())},
         "e2e": {"value": len(q) / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": int(q.nbytes),
                 "d2h_bytes_per_step": int(ih.nbytes + dh.nbytes), "recall_at_10": e2e_rec},
         # per step: routing (query bf16 copy, two tensor-core passes, limit, finish, ids and work
         # order) when entry is "pivot", then the main and second search kernels
-        "gpu_launches": (8 if FORMS[best].get("entry") == "pivot" else 2) * args.steps,
+        "gpu_launches": (8 if FORMS[best].get("entry") in ("pivot", "learned") else 2) * args.steps,
         "clocks": clk,
     }
     if not args.no_serve:

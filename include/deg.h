@@ -168,6 +168,11 @@ DEG_API deg_status deg_export_codes(const deg_index* idx, int32_t precision, voi
  * before deg_upload; DEG_ECUDA on a device error. */
 DEG_API deg_status deg_train_entry(deg_index* idx, int32_t k, int32_t iters, int64_t* sizes_host, void* stream);
 
+/* The routing pivots as caller ids: the sampled ones (learned = 0, chosen at upload) or the learned
+ * ones (learned = 1, deg_train_entry). Returns their number (0 if there are none, -1 on a NULL
+ * index or a device error); ids_host [cap] is filled only when cap is at least that number. */
+DEG_API int32_t deg_get_pivots(const deg_index* idx, int32_t learned, int32_t* ids_host, int32_t cap);
+
 /* The entry vertex computed by deg_upload, or -1 before it. */
 DEG_API int32_t deg_entry_vertex(const deg_index* idx);
 

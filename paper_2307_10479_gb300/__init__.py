@@ -80,6 +80,7 @@ def lib() -> ctypes.CDLL:
             "deg_upload": (S, [P, i32, P]),
             "deg_entry_vertex": (i32, [P]),
             "deg_train_entry": (S, [P, i32, i32, P, P]),
+            "deg_get_pivots": (i32, [P, i32, P, i32]),
             "deg_export_codes": (S, [P, i32, P, P]),
             "deg_free": (None, [P]),
             "deg_search": (S, [P, P, i64, i32, f32, P, P, P, P, P]),
@@ -242,6 +243,16 @@ class Index:
         sizes = np.empty(k, np.int64)
         _check(lib().deg_train_entry(self._h, k, iters, sizes.ctypes.data, _stream_ptr(stream)))
         return sizes
+
+    def pivots(self, learned: bool = False) -> np.ndarray:
+        """The routing pivots (caller ids): sampled at upload, or learned (train_entry)."""
+        n = int(lib().deg_get_pivots(self._h, 1 if learned else 0, None, 0))
+        if n < 0:
+            raise DegError(DEG_ECUDA, "deg_get_pivots failed")
+        out = np.empty(n, np.int32)
+        if n:
+            lib().deg_get_pivots(self._h, 1 if learned else 0, out.ctypes.data, n)
+        return out
 
     @property
     def entry_vertex(self) -> int:

@@ -399,6 +399,22 @@ extern "C" deg_status deg_upload(deg_index* idx, int32_t precision_mask, void* s
 
 extern "C" int32_t deg_entry_vertex(const deg_index* idx) { return idx ? idx->dev.entry : -1; }
 
+extern "C" int32_t deg_get_pivots(const deg_index* idx, int32_t learned, int32_t* ids_host, int32_t cap) {
+    if (!idx) return -1;
+    const DeviceIndex& d = idx->dev;
+    const int32_t* piv = learned ? d.lpivots : d.pivots;
+    const int32_t np = learned ? d.lnpivots : d.npivots;
+    if (!piv) return 0;
+    if (!ids_host || cap < np) return np;
+    // internal ids -> caller ids
+    std::vector<int32_t> in((size_t)np), n2o((size_t)d.n);
+    if (cudaMemcpy(in.data(), piv, sizeof(int32_t) * np, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(n2o.data(), d.new2old, sizeof(int32_t) * d.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    for (int32_t i = 0; i < np; ++i) ids_host[i] = n2o[in[i]];
+    return np;
+}
+
 extern "C" deg_status deg_train_entry(deg_index* idx, int32_t k, int32_t iters, int64_t* sizes_host, void* stream) {
     if (!idx) return fail(DEG_EINVAL, "deg_train_entry: NULL index");
     if (!idx->dev.x32) return fail(DEG_ENOTREADY, "deg_train_entry: upload the index first");

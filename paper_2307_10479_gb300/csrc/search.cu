@@ -56,6 +56,9 @@ constexpr int kMaxDegree = 128;
 #ifndef DEG_SEARCH_FRONT
 #define DEG_SEARCH_FRONT 128
 #endif
+#ifndef DEG_SEARCH_QUERY_IN_SMEM
+#define DEG_SEARCH_QUERY_IN_SMEM 0
+#endif
 #ifndef DEG_SEARCH_ROW_PREFETCH_BYTES
 #define DEG_SEARCH_ROW_PREFETCH_BYTES 256
 #endif
@@ -255,19 +258,30 @@ struct Engine {
     static constexpr int UR = kRows / RP > 0 ? kRows / RP : 1;             // passes for kRows rows
     static constexpr int UC = kBuf / CPL > 0 ? kBuf / CPL : 1;             // register cap
     static constexpr int U = UR < UC ? UR : UC;                            // passes in flight
+#if DEG_SEARCH_QUERY_IN_SMEM
+    const float* qs;                                                       // the query in shared memory
+#else
     float q[CPL][EPC];
+#endif
     float qq;                                                              // ||q||^2 (FP8 expansion)
 
+    // qv: the query in shared memory, zero padded to a multiple of 16 floats
     __device__ void load_query(const float* qv, int dim, int lane) {
         const int p = lane % G;
         float s = 0.f;
+#if DEG_SEARCH_QUERY_IN_SMEM
+        qs = qv;
+#endif
 #pragma unroll
         for (int j = 0; j < CPL; ++j)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
                 const int i = (p + G * j) * EPC + e;
-                q[j][e] = i < dim ? qv[i] : 0.f;
-                s = fmaf(q[j][e], q[j][e], s);
+                const float v = i < dim ? qv[i] : 0.f;
+#if !DEG_SEARCH_QUERY_IN_SMEM
+                q[j][e] = v;
+#endif
+                s = fmaf(v, v, s);
             }
 #pragma unroll
         for (int m = G / 2; m; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);  // one lane group holds all of q
@@ -303,7 +317,23 @@ struct Engine {
                     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                     for (int j = 0; j < CPL; ++j)
-                        if (p + G * j < P.nchunk) Rows::acc(buf[u][j], q[j], a0, a1);
+                        if (p + G * j < P.nchunk) {
+#if DEG_SEARCH_QUERY_IN_SMEM
+                            float qr[EPC];
+                            const float4* q4 = reinterpret_cast<const float4*>(qs + (p + G * j) * EPC);
+#pragma unroll
+                            for (int e = 0; e < EPC / 4; ++e) {
+                                const float4 t = q4[e];
+                                qr[4 * e] = t.x;
+                                qr[4 * e + 1] = t.y;
+                                qr[4 * e + 2] = t.z;
+                                qr[4 * e + 3] = t.w;
+                            }
+                            Rows::acc(buf[u][j], qr, a0, a1);
+#else
+                            Rows::acc(buf[u][j], q[j], a0, a1);
+#endif
+                        }
                     float a = a0 + a1;
 #pragma unroll
                     for (int m = G / 2; m; m >>= 1) a += __shfl_xor_sync(0xffffffffu, a, m);
@@ -788,8 +818,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     const int32_t seed = !given ? P.entry : (!seed_ok ? 0 : P.seeds_internal ? seed_in : __ldg(P.old2new + seed_in));
     const int32_t seed_c = !given ? P.entry_caller : (!seed_ok ? 0 : P.seeds_internal ? __ldg(P.new2old + seed_in) : seed_in);
     const float* qsrc = P.explore ? P.x32 + (int64_t)(seed_ok ? seed : 0) * P.dim_pad : P.queries + (int64_t)q * P.dim;
-    const int dim4 = (P.dim + 3) / 4 * 4;
-    for (int i = lane; i < dim4; i += 32) qv_smem[i] = i < P.dim ? qsrc[i] : 0.f;
+    const int dim16 = (P.dim + 15) / 16 * 16;                  // zero padded to whole 16-element chunks
+    for (int i = lane; i < dim16; i += 32) qv_smem[i] = i < P.dim ? qsrc[i] : 0.f;
     W.fn = W.back_n = W.res_n = 0;
     W.wmark = kEmptyKey;
     W.trimmed = false;
@@ -958,7 +988,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
 
 // Shared-memory bytes per warp.
 __host__ __device__ inline int64_t warp_bytes(int kcap, int dim) {
-    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 3) / 4 * 4);
+    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 15) / 16 * 16);
     return (b + 15) / 16 * 16;
 }
 
@@ -1104,7 +1134,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
     W.tn = 0;
     W.back = P.backs + (int64_t)slot * P.bstride;
     W.bcap = P.bcap;
-    const int dim4 = (P.dim + 3) / 4 * 4;
+    const int dim16 = (P.dim + 15) / 16 * 16;
     for (;;) {
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(S.claim, 1ull);
@@ -1146,7 +1176,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
             Q.queries = S.vecs + (int64_t)r * P.dim;
             Q.seeds = nullptr;
             if (S.entry_mode >= 1) {
-                for (int d = lane; d < dim4; d += 32) qv[d] = d < P.dim ? Q.queries[d] : 0.f;
+                for (int d = lane; d < dim16; d += 32) qv[d] = d < P.dim ? Q.queries[d] : 0.f;
                 __syncwarp();
                 const int32_t sd = route_one(P, pivots, np, qv, lane);
                 if (lane == 0) seed_s[warp] = sd;

@@ -562,6 +562,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the k = 1 / 100 and exploration points")
+    ap.add_argument("--only", default=None, choices=["plain", "fp8-pivot", "fp8-learned", "bf16-learned"],
+                    help="run one form at --eps for --warmup + --steps batches and nothing else (for profilers)")
     ap.add_argument("--train-queries", type=int, default=100_000, help="held-out queries traced for the stop network")
     ap.add_argument("--builder", default="host", choices=["host", "device"],
                     help="graph builder when the workload's graph file is missing")
@@ -602,6 +604,18 @@ def main():
     n, dim, degree = idx.info()
     log(f"[bench] index {n} x {dim}, d={degree}, entry {idx.entry_vertex}, setup {time.time() - t0:.1f} s")
     qd = torch.from_numpy(q).cuda()
+    if args.only:
+        # one form at a fixed eps, nothing else: the launches a profiler captures
+        form = {"plain": dict(precision="f32", entry="fixed"),
+                "fp8-pivot": dict(precision="fp8", rerank=args.rerank, entry="pivot"),
+                "fp8-learned": dict(precision="fp8", rerank=args.rerank, entry="learned"),
+                "bf16-learned": dict(precision="bf16", rerank=args.rerank, entry="learned")}[args.only]
+        if form["entry"] == "learned":
+            idx.train_entry(len(idx.pivots()), 10)
+        eps = args.eps if args.eps is not None else OPERATING_EPS
+        ms = time_steps(lambda: idx.search(qd, k=K, eps=eps, **form), args.steps, args.warmup, torch.cuda.current_stream())
+        print(json.dumps({"only": args.only, "eps": eps, "steps": args.steps, "ms_per_step": sum(ms) / len(ms)}), flush=True)
+        return
     # ground truth (Eq. 1) by the library's exact k-NN, timed as the tensor-core row of the path
     bq = torch.from_numpy(base).cuda()
     deg.knn_exact(bq, qd[:256], K)

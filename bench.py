@@ -415,13 +415,19 @@ def serving(deg, idx, w, q, gt):
             arrivals = synth.poisson_arrivals(rate, n, seed=4 + rate)
             arrivals -= arrivals[0]
             t0 = time.perf_counter()
-            lat, ids, _, st = srv.run_trace(q[qi], vertices, ks, epss, arrivals, timeout_s=300.0)
+            lat, ids, _, st, dev = srv.run_trace(q[qi], vertices, ks, epss, arrivals, timeout_s=300.0, device_times=True)
             wall = time.perf_counter() - t0
             vec10 = (~explore) & (ks >= 10)
             rec = recall(ids[vec10, :10], gt[qi[vec10]])
             out["rates"][str(rate)] = {"offered_qps": rate, "sustained_qps": n / wall, "p50_ms": 1e3 * float(np.median(lat)),
                                        "p99_ms": 1e3 * float(np.percentile(lat, 99)), "recall_at_10": rec,
-                                       "status_ok": bool((st == 0).all())}
+                                       "status_ok": bool((st == 0).all()),
+                                       # latency = device time (a warp running the request) + the rest
+                                       # (posting, waiting for a warp, collection by the host)
+                                       "device_p50_ms": 1e3 * float(np.median(dev)),
+                                       "device_p99_ms": 1e3 * float(np.percentile(dev, 99)),
+                                       "rest_p50_ms": 1e3 * float(np.median(lat - dev)),
+                                       "rest_p99_ms": 1e3 * float(np.percentile(lat - dev, 99))}
             log(f"[bench] serving {rate}/s: sustained {n / wall:.0f}/s, p50 {1e3 * np.median(lat):.2f} ms, "
                 f"p99 {1e3 * np.percentile(lat, 99):.2f} ms, recall@10 {rec:.4f}")
     finally:

@@ -322,11 +322,14 @@ DEG_API int32_t deg_serve_poll(deg_server* srv, int64_t seq, int32_t* ids_host, 
  * as soon as its ring slot frees), results go to ids_out / dists_out [count][kmax] and
  * status_out [count], and latency_s_out[i] = completion time - arrival_s[i] as seen by the host.
  * vecs_host [count][dim] (rows of exploration requests are ignored), vertices [count] (-1 for a
- * vector query), ks [count], epss [count]. Fails with DEG_ETIMEOUT after timeout_s seconds. */
+ * vector query), ks [count], epss [count]. Fails with DEG_ETIMEOUT after timeout_s seconds.
+ * device_s_out (nullable) [count] gets each request's device time: from the warp taking the posted
+ * request to its result being published (%globaltimer), so latency minus device time is the time
+ * spent waiting to be posted, waiting for a free warp and being collected by the host. */
 DEG_API deg_status deg_serve_run_trace(deg_server* srv, const float* vecs_host, const int32_t* vertices,
                                        const int32_t* ks, const float* epss, const double* arrival_s, int64_t count,
                                        double* latency_s_out, int32_t* ids_out, float* dists_out,
-                                       int32_t* status_out, double timeout_s);
+                                       int32_t* status_out, double* device_s_out, double timeout_s);
 
 /* Number of warps (concurrent requests) of the running kernel. */
 DEG_API int32_t deg_serve_slots(const deg_server* srv);

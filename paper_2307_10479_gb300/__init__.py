@@ -100,7 +100,7 @@ def lib() -> ctypes.CDLL:
             "deg_serve_start": (S, [P, ctypes.POINTER(ServeConfig), ctypes.POINTER(P)]),
             "deg_serve_submit": (S, [P, P, i32, i32, f32, ctypes.POINTER(i64)]),
             "deg_serve_poll": (i32, [P, i64, P, P, P]),
-            "deg_serve_run_trace": (S, [P, P, P, P, P, P, i64, P, P, P, P, ctypes.c_double]),
+            "deg_serve_run_trace": (S, [P, P, P, P, P, P, i64, P, P, P, P, P, ctypes.c_double]),
             "deg_serve_slots": (i32, [P]),
             "deg_serve_stop": (S, [P]),
             "deg_last_error": (ctypes.c_char_p, []),
@@ -368,7 +368,8 @@ class Server:
             _check(got)
         return (ids, d, st.value) if got == 1 else None
 
-    def run_trace(self, vecs, vertices, ks, epss, arrival_s, timeout_s: float = 120.0):
+    def run_trace(self, vecs, vertices, ks, epss, arrival_s, timeout_s: float = 120.0, device_times: bool = False):
+        """Replay an arrival trace; returns (latency_s, ids, dists, status[, device_s])."""
         vecs = np.ascontiguousarray(vecs, np.float32)
         vertices = np.ascontiguousarray(vertices, np.int32)
         ks = np.ascontiguousarray(ks, np.int32)
@@ -379,10 +380,12 @@ class Server:
         ids = np.full((n, self.kmax), -1, np.int32)
         d = np.full((n, self.kmax), np.inf, np.float32)
         st = np.empty(n, np.int32)
+        dev = np.zeros(n, np.float64) if device_times else None
         _check(lib().deg_serve_run_trace(self._h, vecs.ctypes.data, vertices.ctypes.data, ks.ctypes.data,
                                          epss.ctypes.data, arrival_s.ctypes.data, n, lat.ctypes.data, ids.ctypes.data,
-                                         d.ctypes.data, st.ctypes.data, float(timeout_s)))
-        return lat, ids, d, st
+                                         d.ctypes.data, st.ctypes.data, None if dev is None else dev.ctypes.data,
+                                         float(timeout_s)))
+        return (lat, ids, d, st, dev) if device_times else (lat, ids, d, st)
 
     def stop(self):
         h, self._h = self._h, None

@@ -722,6 +722,7 @@ struct deg_server {
     int32_t* status = nullptr;
     int32_t* trace = nullptr;
     uint32_t* done = nullptr;
+    unsigned long long* times = nullptr;   // [cap][2] device start / end of each request (ns)
     unsigned long long* tail = nullptr;
     int32_t* stop = nullptr;
     // device words
@@ -736,7 +737,7 @@ namespace {
 void server_free(deg_server* s) {
     cudaFreeHost(s->vecs); cudaFreeHost(s->meta); cudaFreeHost(s->ids); cudaFreeHost(s->dists);
     cudaFreeHost(s->status); cudaFreeHost(s->trace); cudaFreeHost(s->done); cudaFreeHost(s->tail);
-    cudaFreeHost(s->stop);
+    cudaFreeHost(s->stop); cudaFreeHost(s->times);
     cudaFree(s->kstatus); cudaFree(s->claim);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -783,7 +784,8 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
     if ((e = host_alloc(&s->vecs, cap * s->dim)) != cudaSuccess || (e = host_alloc(&s->meta, cap * 4)) != cudaSuccess ||
         (e = host_alloc(&s->ids, cap * s->kmax)) != cudaSuccess || (e = host_alloc(&s->dists, cap * s->kmax)) != cudaSuccess ||
         (e = host_alloc(&s->status, cap)) != cudaSuccess || (e = host_alloc(&s->trace, cap * 4)) != cudaSuccess ||
-        (e = host_alloc(&s->done, cap)) != cudaSuccess || (e = host_alloc(&s->tail, 1)) != cudaSuccess ||
+        (e = host_alloc(&s->done, cap)) != cudaSuccess || (e = host_alloc(&s->times, 2 * cap)) != cudaSuccess ||
+        (e = host_alloc(&s->tail, 1)) != cudaSuccess ||
         (e = host_alloc(&s->stop, 1)) != cudaSuccess || (e = cudaMalloc(&s->kstatus, 4)) != cudaSuccess ||
         (e = cudaMalloc(&s->claim, 8)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -797,10 +799,11 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
         return cuda_fail(e, "serve_start");
     }
     ServeArgs a{&idx->dev, dev_view(s->vecs), dev_view(s->meta), dev_view(s->ids), dev_view(s->dists),
-                dev_view(s->status), dev_view(s->trace), dev_view(s->done), dev_view(s->tail), dev_view(s->stop),
+                dev_view(s->status), dev_view(s->trace), dev_view(s->done), dev_view(s->times), dev_view(s->tail),
+                dev_view(s->stop),
                 s->kstatus, s->claim, s->cap, s->kmax, cfg->entry_mode, cfg->precision, cfg->rerank,
                 cfg->learned_stop ? 1 : 0, (unsigned long long)(cfg->idle_timeout_s * 1e9)};
-    if (!a.vecs || !a.meta || !a.ids || !a.dists || !a.status || !a.trace || !a.done || !a.tail || !a.stop) {
+    if (!a.vecs || !a.meta || !a.ids || !a.dists || !a.status || !a.trace || !a.done || !a.times || !a.tail || !a.stop) {
         server_free(s);
         return fail(DEG_ECUDA, "serve_start: no device view of the mapped ring");
     }
@@ -839,6 +842,14 @@ extern "C" deg_status deg_serve_submit(deg_server* s, const float* vec_host, int
     return DEG_OK;
 }
 
+// A finished request's device time (from taking it to publishing it), read after its completion was
+// seen and before its ring slot takes another request.
+static double device_seconds(const deg_server* s, size_t r) {
+    const unsigned long long a = __atomic_load_n(s->times + 2 * r, __ATOMIC_ACQUIRE);
+    const unsigned long long b = __atomic_load_n(s->times + 2 * r + 1, __ATOMIC_ACQUIRE);
+    return b >= a ? (double)(b - a) * 1e-9 : 0.0;
+}
+
 extern "C" int32_t deg_serve_poll(deg_server* s, int64_t seq, int32_t* ids_host, float* dists_host,
                                   int32_t* status_host) {
     if (!s || seq < 0 || seq >= s->posted) return fail(DEG_EINVAL, "serve_poll: unknown request");
@@ -856,7 +867,7 @@ extern "C" int32_t deg_serve_poll(deg_server* s, int64_t seq, int32_t* ids_host,
 extern "C" deg_status deg_serve_run_trace(deg_server* s, const float* vecs_host, const int32_t* vertices,
                                           const int32_t* ks, const float* epss, const double* arrival_s, int64_t count,
                                           double* latency_s_out, int32_t* ids_out, float* dists_out,
-                                          int32_t* status_out, double timeout_s) {
+                                          int32_t* status_out, double* device_s_out, double timeout_s) {
     if (!s || !vecs_host || !vertices || !ks || !epss || !arrival_s || !latency_s_out || count < 0)
         return fail(DEG_EINVAL, "serve_run_trace: NULL argument");
     using clk = std::chrono::steady_clock;
@@ -891,6 +902,7 @@ extern "C" deg_status deg_serve_run_trace(deg_server* s, const float* vecs_host,
             if (got == 1) {
                 latency_s_out[i] = now() - arrival_s[i];
                 if (status_out) status_out[i] = stv;
+                if (device_s_out) device_s_out[i] = device_seconds(s, (size_t)(seq_of[i] % s->cap));
                 ++finished;
                 outstanding[j] = outstanding.back();
                 outstanding.pop_back();

@@ -132,6 +132,7 @@ struct ServeArgs {
     int32_t* status;
     int32_t* trace;
     uint32_t* done;
+    unsigned long long* times;    // [cap][2] device start / end (%globaltimer ns)
     const unsigned long long* tail;
     const int32_t* stop;
     int32_t* kstatus;

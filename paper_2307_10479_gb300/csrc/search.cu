@@ -1084,6 +1084,7 @@ struct ServeRing {
     int32_t* status;                      // [cap]
     int32_t* trace;                       // [cap][4]
     uint32_t* done;                       // [cap]: seq + 1 once the result is written
+    unsigned long long* times;            // [cap][2]: %globaltimer when the request was taken, when done
     const unsigned long long* tail;       // requests posted so far
     const int32_t* stop;
     int32_t* kstatus;                     // kernel status (device memory)
@@ -1139,21 +1140,29 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
         unsigned long long i = 0;
         if (lane == 0) i = atomicAdd(S.claim, 1ull);
         i = __shfl_sync(0xffffffffu, i, 0);
-        // wait until request i is posted, the host asks to stop, or nothing arrives for idle_ns
+        // wait until request i is posted, the host asks to stop, or nothing arrives for idle_ns. The
+        // ring lives in host memory, and thousands of waiting warps polling it back to back load
+        // the link to it: the wait backs off from 256 ns to 4 us, and the stop flag is read on
+        // every eighth poll only.
         const unsigned long long t0 = global_ns();
         int state = 0;                                        // 1 posted, 2 stop, 3 timeout
-        while (state == 0) {
+        unsigned sleep_ns = 256;
+        for (unsigned poll = 0; state == 0; ++poll) {
             if (lane == 0) {
                 if (ld_acquire_sys(S.tail) > i) state = 1;
-                else if (ld_acquire_sys(S.stop)) state = 2;
+                else if ((poll & 7) == 7 && ld_acquire_sys(S.stop)) state = 2;
                 else if (global_ns() - t0 > S.idle_ns) state = 3;
             }
             state = __shfl_sync(0xffffffffu, state, 0);
-            if (state == 0) __nanosleep(500);
+            if (state == 0) {
+                __nanosleep(sleep_ns);
+                sleep_ns = min(sleep_ns * 2, 4096u);
+            }
         }
         if (state == 3 && lane == 0) atomicExch(S.kstatus, (int)DEG_ETIMEOUT);
         if (state != 1) return;
         const int r = (int)(i % (unsigned long long)S.cap);
+        if (lane == 0) S.times[2 * r] = global_ns();
         const int4 m = S.meta[r];
         Params Q = P;
         Q.k = m.x;
@@ -1192,6 +1201,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
             if (lane == 0) *Q.status = DEG_EOVERFLOW;
         }
         __syncwarp();
+        if (lane == 0) S.times[2 * r + 1] = global_ns();
         __threadfence_system();
         if (lane == 0) st_release_sys(S.done + r, (uint32_t)(i + 1));
     }
@@ -1478,7 +1488,7 @@ int launch_serving(const ServeArgs& a, Workspace& ws, deg_stream_t stream, int* 
     const int32_t* piv = a.entry_mode == 2 ? ix.lpivots : ix.pivots;
     const int32_t npiv = a.entry_mode == 2 ? ix.lnpivots : ix.npivots;
     if (a.entry_mode == 2 && !piv) return *why = "no learned entry points (deg_train_entry)", (int)cudaErrorInvalidValue;
-    ServeRing S{a.vecs, reinterpret_cast<const int4*>(a.meta), a.ids, a.dists, a.status, a.trace, a.done, a.tail,
+    ServeRing S{a.vecs, reinterpret_cast<const int4*>(a.meta), a.ids, a.dists, a.status, a.trace, a.done, a.times, a.tail,
                 a.stop, a.kstatus, a.claim, a.cap, a.kmax, a.entry_mode, a.idle_ns};
     if (a.precision == DEG_F32) {
         P.rows = reinterpret_cast<const uint8_t*>(ix.x32);

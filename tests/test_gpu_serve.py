@@ -41,9 +41,11 @@ def test_results_in_the_mix_equal_results_alone(index, precision, entry):
     q, vertices, ks, epss = _requests(400, 11)
     srv = deg.Server(idx, capacity=1024, kmax=128, precision=precision, entry=entry, idle_timeout_s=30.0)
     assert srv.slots > 0
-    lat, ids, dists, st = srv.run_trace(q, vertices, ks, epss, np.zeros(len(ks)))   # all at once
+    lat, ids, dists, st, dev = srv.run_trace(q, vertices, ks, epss, np.zeros(len(ks)), device_times=True)  # all at once
     srv.stop()
     assert (st == 0).all() and (lat >= 0).all()
+    # device time: a warp's time on the request, within the request's whole latency
+    assert (dev > 0).all() and (dev <= lat + 1e-3).all()
     for i in range(len(ks)):
         k, eps = int(ks[i]), float(epss[i])
         if vertices[i] >= 0:

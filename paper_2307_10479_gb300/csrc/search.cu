@@ -22,12 +22,12 @@
 // bitmap use internal ids (the locality layout), which the adjacency carries beside each caller id.
 //
 // State of one query. The checked set C is an n-bit bitmap in the warp's slot of device memory
-// (cleared when the query starts). S is split in two: a "front" of at most F keys kept sorted
-// (descending) in shared memory, and a "back" pool of keys in the warp's device-memory slot, with
-// a watermark w such that every front key < w <= every back key. So the front's last key is the
-// minimum of S: a pop costs one shared-memory read. A new candidate below w goes into the front
-// (evicting the front's largest key to the back when full, which becomes the new w); one at or
-// above w is appended to the back. When the front runs empty, it is refilled with the F
+// (cleared when the query starts). S is split in two: an unsorted "front" of at most F keys in
+// shared memory, and a "back" pool of keys in the warp's device-memory slot, with a watermark w
+// such that every front key < w <= every back key. So the front's minimum, found by a warp
+// reduction, is the minimum of S. New candidates below w are appended to the front (the front's
+// largest keys over F move to the back, and the smallest of them becomes the new w); those at or
+// above w are appended to the back. When the front runs empty, it is refilled with the F
 // smallest back keys, found exactly by an 8-bit-digit radix select over the 64-bit keys, and
 // back keys above the current admission radius are dropped on the way (a candidate with
 // d > r(1+eps) can never pass the stop test again, since r only shrinks). R is a sorted array
@@ -229,8 +229,7 @@ struct WarpState {
     int32_t* touched;          // ids visited by this query (main and serving kernels), or null
     int32_t tn;                // their number (above kTouchCap: clear the whole bitmap)
     uint64_t* fbuf;            // 32 keys of scratch for batched admission
-    uint64_t* front;           // S, smallest part, sorted descending, [kFront]
-    uint64_t* front2;          // the other front buffer (a batched merge writes it, then they swap)
+    uint64_t* front;           // S, smallest part, unsorted, [kFront + 32] (a batch appends before the trim)
     uint64_t* back;            // S, the rest (device memory), [bcap]
     uint64_t* res;             // R, sorted ascending
     int32_t* cid;              // per-hop candidate internal ids [kMaxDegree] (also the refill histogram)
@@ -402,10 +401,36 @@ __device__ __forceinline__ void result_insert(WarpState& W, int ks, uint64_t c, 
     }
 }
 
+// The front of S is unsorted: its minimum (the next pop) and its maximum (the key to evict) are
+// found by a warp reduction. Keys are unique (a vertex enters S at most once), so the extreme key
+// names its slot. fn > 0.
+__device__ __forceinline__ int front_extreme(const WarpState& W, bool want_max, uint64_t* out, int lane) {
+    uint64_t best = want_max ? 0ull : kEmptyKey;
+    int bi = -1;
+    for (int i = lane; i < W.fn; i += 32) {
+        const uint64_t v = W.front[i];
+        if (want_max ? v >= best : v <= best) {
+            best = v;
+            bi = i;
+        }
+    }
+    uint64_t m = best;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)m, o);
+        const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(m >> 32), o);
+        const uint64_t t = ((uint64_t)hi << 32) | lo;
+        m = want_max ? max(m, t) : min(m, t);
+    }
+    const unsigned own = __ballot_sync(0xffffffffu, bi >= 0 && best == m);
+    *out = m;
+    return __shfl_sync(0xffffffffu, bi, __ffs(own) - 1);
+}
+
 // ---- learned early stop -------------------------------------------------------------------
 // Twelve warp-uniform features of the search state after a hop (the same code makes the
 // training traces and feeds the network during a search).
-__device__ __forceinline__ float stop_feature(const WarpState& W, int i, float d2_pop, int cnt, int adm, float f) {
+__device__ __forceinline__ float stop_feature(const WarpState& W, int i, float d2_pop, int cnt, int adm, float f, int lane) {
     const float inf = __int_as_float(0x7f800000);
     switch (i) {
         case 0: return W.hops * (1.f / 64.f);
@@ -415,7 +440,9 @@ __device__ __forceinline__ float stop_feature(const WarpState& W, int i, float d
         case 4: return W.trimmed ? d2_pop / W.r2 : 0.f;
         case 5: {
             if (!W.trimmed) return 0.f;
-            const float nxt = W.fn > 0 ? key_d2(W.front[W.fn - 1]) : (W.back_n > 0 ? key_d2(W.wmark) : inf);
+            uint64_t fmin = kEmptyKey;
+            if (W.fn > 0) front_extreme(W, false, &fmin, lane);
+            const float nxt = W.fn > 0 ? key_d2(fmin) : (W.back_n > 0 ? key_d2(W.wmark) : inf);
             return fminf(nxt / (W.r2 * f), 4.f);
         }
         case 6: return fminf((float)(W.hops - W.last_change), 256.f) * (1.f / 16.f);
@@ -488,61 +515,44 @@ __device__ __forceinline__ bool back_push(WarpState& W, uint64_t c, const Radius
     return true;
 }
 
+// Move front keys to the back pool, largest first, until the front holds kFront keys; wmark
+// follows the smallest evicted key, so every front key < wmark <= every back key still holds.
+// False if the back pool overflowed.
+__device__ __forceinline__ bool trim_front(WarpState& W, const Radius& thr, int lane) {
+    while (W.fn > kFront) {
+        uint64_t kmax;
+        const int i = front_extreme(W, true, &kmax, lane);
+        __syncwarp();
+        if (lane == 0) W.front[i] = W.front[W.fn - 1];
+        --W.fn;
+        __syncwarp();
+        W.wmark = min(W.wmark, kmax);
+        if (!back_push(W, kmax, thr, lane)) return false;
+    }
+    return true;
+}
+
 // Add candidate c (admitted to S). False if the back pool overflowed.
 __device__ __forceinline__ bool s_insert(WarpState& W, uint64_t c, const Radius& thr, int lane) {
     if (c >= W.wmark) return back_push(W, c, thr, lane);
-    // position in the descending front: number of keys greater than c
-    int pos = 0;
-    for (int i0 = 0; i0 < W.fn; i0 += 32) {
-        const int i = i0 + lane;
-        pos += __popc(__ballot_sync(0xffffffffu, i < W.fn && W.front[i] > c));
-    }
-    if (W.fn < kFront) {
-        // shift [pos, fn) up by one, top chunk first
-        for (int c0 = pos + ((W.fn - 1 - pos) / 32) * 32; W.fn > pos && c0 >= pos; c0 -= 32) {
-            const int i = c0 + lane;
-            const uint64_t v = i < W.fn ? W.front[i] : 0;
-            __syncwarp();
-            if (i < W.fn) W.front[i + 1] = v;
-            __syncwarp();
-        }
-        if (lane == 0) W.front[pos] = c;
-        ++W.fn;
-        __syncwarp();
-        return true;
-    }
-    if (pos == 0) {                                           // c above every front key
-        W.wmark = c;
-        return back_push(W, c, thr, lane);
-    }
-    // full: evict the largest key front[0] to the back, shift [1, pos) down, place c at pos-1
-    const uint64_t evicted = W.front[0];
-    for (int c0 = 1; c0 < pos; c0 += 32) {
-        const int i = c0 + lane;
-        const uint64_t v = i < pos ? W.front[i] : 0;
-        __syncwarp();
-        if (i < pos) W.front[i - 1] = v;
-        __syncwarp();
-    }
-    if (lane == 0) W.front[pos - 1] = c;
+    if (lane == 0) W.front[W.fn] = c;
+    ++W.fn;
     __syncwarp();
-    W.wmark = evicted;
-    return back_push(W, evicted, thr, lane);
+    return trim_front(W, thr, lane);
 }
 
-// Admit a batch of candidates (one per lane, where `take`) to S at once: merge them with the
-// sorted front, the largest overflow keys go to the back pool, and wmark becomes the smallest of
-// those. S ends as the same set as after one-by-one insertion, and every front key stays below
-// wmark <= every back key, so pops are unchanged. A batch that would overflow the back pool takes
-// the one-by-one path (which compacts the pool). False if the pool overflowed.
+// Admit a batch of candidates (one per lane, where `take`) to S at once: keys below wmark are
+// appended to the front, the others to the back pool, then the front's largest keys over its
+// capacity move to the back pool. S ends as the same set as after one-by-one insertion and pops
+// take its minimum, so pops are unchanged. A batch that could overflow the back pool takes the
+// one-by-one path (which compacts the pool). False if the pool overflowed.
 __device__ bool admit_batch(WarpState& W, uint64_t key, bool take, const Radius& thr, int lane) {
     const unsigned all = __ballot_sync(0xffffffffu, take);
     if (!all) return true;
     const bool toF = take && key < W.wmark;
     const unsigned mf = __ballot_sync(0xffffffffu, toF), mb = all & ~mf;
-    const int m = __popc(mf), nb = __popc(mb), fn = W.fn;
-    const int E = max(0, fn + m - kFront);                    // evicted: the E largest of the merge
-    if (W.back_n + nb + E > W.bcap) {
+    const int m = __popc(mf), nb = __popc(mb);
+    if (W.back_n + nb + m > W.bcap) {
         unsigned rest = all;
         while (rest) {
             const int src = __ffs(rest) - 1;
@@ -552,52 +562,11 @@ __device__ bool admit_batch(WarpState& W, uint64_t key, bool take, const Radius&
         return true;
     }
     if (take && !toF) W.back[W.back_n + __popc(mb & lanes_below(lane))] = key;
-    if (m > 0) {
-        uint64_t* fb = W.fbuf;
-        if (toF) fb[__popc(mf & lanes_below(lane))] = key;
-        __syncwarp();
-        int knew = -1;                                        // merged (descending) index of key
-        if (toF) {
-            int r = 0;
-            for (int j = 0; j < m; ++j) r += fb[j] > key;
-            int lo = 0;                                       // front keys above key (fixed steps)
-#pragma unroll
-            for (int step = kFront; step; step >>= 1)
-                if (lo + step <= fn && W.front[lo + step - 1] > key) lo += step;
-            knew = r + lo;
-        }
-        // the merge goes to the second buffer (the first is still read), which then becomes the front.
-        // The new keys' merged indices, as a bit mask one 32-index word at a time, place the front
-        // keys: merged index p that no new key holds takes front key p - (new keys below p).
-        const int64_t ev0 = W.back_n + nb;                    // evicted keys land after the direct ones
-        const int total = fn + m;                             // <= kFront + 32
-        uint64_t last = kEmptyKey;                            // merged index E - 1: the new wmark
-        uint64_t* dst = W.front2;
-        int below = 0;                                        // new keys at merged indices under word c
-#pragma unroll
-        for (int c = 0; c < kFront / 32 + 1; ++c) {
-            if (32 * c >= total) break;                       // warp-uniform
-            const unsigned word = __reduce_or_sync(0xffffffffu, (knew >> 5) == c ? 1u << (knew & 31) : 0u);
-            const int p = 32 * c + lane;
-            if (p < total && !((word >> lane) & 1u)) {
-                const uint64_t v = W.front[p - below - __popc(word & lanes_below(lane))];
-                if (p >= E) dst[p - E] = v;
-                else W.back[ev0 + p] = v;
-                if (p == E - 1) last = v;
-            }
-            below += __popc(word);
-        }
-        if (knew >= E) dst[knew - E] = key;
-        else if (knew >= 0) W.back[ev0 + knew] = key;
-        if (toF && knew == E - 1) last = key;
-        if (E > 0) W.wmark = warp_min64(last);
-        W.front2 = W.front;
-        W.front = dst;
-    }
-    W.fn = fn + m - E;
-    W.back_n += nb + E;
+    if (toF) W.front[W.fn + __popc(mf & lanes_below(lane))] = key;
+    W.back_n += nb;
+    W.fn += m;
     __syncwarp();
-    return true;
+    return trim_front(W, thr, lane);
 }
 
 // Add a batch of result candidates (one per lane, where `take`) to R, sorted ascending: merge,
@@ -735,19 +704,7 @@ __device__ void refill(WarpState& W, const Radius& thr, int lane) {
     W.fn = fo;
     W.back_n = bo;
     W.wmark = warp_min64(wm);
-    // sort the front descending (bitonic over kFront slots, padded with key 0, the smallest)
-    for (int i = fo + lane; i < kFront; i += 32) W.front[i] = 0;
-    __syncwarp();
-    for (int size = 2; size <= kFront; size <<= 1)
-        for (int stride = size >> 1; stride; stride >>= 1) {
-            for (int t = lane; t < kFront / 2; t += 32) {
-                const int lo = 2 * t - (t & (stride - 1)), hi = lo + stride;
-                const bool desc = (lo & size) == 0;
-                const uint64_t a = W.front[lo], b = W.front[hi];
-                if ((a < b) == desc) { W.front[lo] = b; W.front[hi] = a; }
-            }
-            __syncwarp();
-        }
+    // the front is unsorted: pops take its minimum
 }
 
 // Re-rank if asked, then write R (already sorted) to the outputs.
@@ -874,10 +831,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             if (lane == 0) visit(W.bitmap, s2);
             __syncwarp();
             const uint64_t k2 = make_key(W.cd2[0], s2c);
-            if (lane == 0) {                                  // the front stays sorted descending
-                if (k2 < W.front[0]) W.front[1] = k2;
-                else { W.front[1] = W.front[0]; W.front[0] = k2; }
-            }
+            if (lane == 0) W.front[1] = k2;
             W.fn = 2;
             W.peak = 2;
             W.evals = 2;
@@ -897,10 +851,13 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             refill(W, thr, lane);
             if (W.fn == 0) break;
         }
-        // 1. pop the minimum of S (the front's last key)
-        const uint64_t m = W.front[W.fn - 1];
+        // 1. pop the minimum of S (the front's minimum)
+        uint64_t m;
+        const int mi = front_extreme(W, false, &m, lane);
         if (!thr.admits(key_d2(m))) break;                     // too far: return R
         if (P.max_hops && W.hops >= P.max_hops) { status = DEG_EHOPLIMIT; break; }
+        __syncwarp();
+        if (lane == 0) W.front[mi] = W.front[W.fn - 1];
         --W.fn;
         ++W.hops;
         const int32_t s = key_id(m);                           // caller id: the adjacency row
@@ -972,7 +929,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         if (ask || P.rec_feats) {
             float x[kStopFeatures];
 #pragma unroll
-            for (int i = 0; i < kStopFeatures; ++i) x[i] = stop_feature(W, i, key_d2(m), cnt, adm, P.f);
+            for (int i = 0; i < kStopFeatures; ++i) x[i] = stop_feature(W, i, key_d2(m), cnt, adm, P.f, lane);
             if (P.rec_feats && W.hops <= P.rec_cap && lane < kStopFeatures) {
                 float v = x[0];
 #pragma unroll
@@ -988,14 +945,13 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
 
 // Shared-memory bytes per warp.
 __host__ __device__ inline int64_t warp_bytes(int kcap, int dim) {
-    const int64_t b = 16ll * kFront + 8ll * kcap + (4 + 4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 15) / 16 * 16);
+    const int64_t b = 8ll * (kFront + 32) + 8ll * kcap + (4 + 4 + 4) * kMaxDegree + 8ll * 32 + 4ll * ((dim + 15) / 16 * 16);
     return (b + 15) / 16 * 16;
 }
 
 __device__ __forceinline__ float* bind_smem(WarpState& W, uint8_t* base, const Params& P) {
     W.front = reinterpret_cast<uint64_t*>(base);
-    W.front2 = W.front + kFront;
-    W.res = W.front2 + kFront;
+    W.res = W.front + kFront + 32;
     W.cid = reinterpret_cast<int32_t*>(W.res + P.kcap);
     W.cd2 = reinterpret_cast<float*>(W.cid + kMaxDegree);
     W.ccid = reinterpret_cast<int32_t*>(W.cd2 + kMaxDegree);

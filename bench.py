@@ -60,7 +60,7 @@ def measured_peak(key="hbm_gbs", fallback=6800.0):
 def source_digest():
     """Digest of the sources that decide what the search kernels read (kernel, routing)."""
     h = hashlib.sha256()
-    for f in ("search.cu", "layout.cu", "knn_tc.cu"):
+    for f in ("search_impl.cuh", "search.cu", "search_f32.cu", "search_bf16.cu", "search_fp8.cu", "layout.cu", "knn_tc.cu"):
         h.update(open(os.path.join(ROOT, "paper_2307_10479_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

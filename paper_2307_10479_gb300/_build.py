@@ -13,7 +13,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
-SOURCES = ["capi.cu", "search.cu", "entry.cu", "layout.cu", "quantize.cu", "knn_exact.cu", "knn_tc.cu", "mlp.cu", "build_gpu.cu", "builder.cpp"]
+SOURCES = ["capi.cu", "search.cu", "search_f32.cu", "search_bf16.cu", "search_fp8.cu", "entry.cu", "layout.cu", "quantize.cu", "knn_exact.cu", "knn_tc.cu", "mlp.cu", "build_gpu.cu", "builder.cpp"]
 
 
 def _deps():

@@ -904,7 +904,8 @@ inline __device__ void clear_visited(WarpState& W, const Params& P, int lane) {
     __syncwarp();
 }
 
-template <class Rows, int G, int CPL>
+// Mode: 0 the front of S unsorted, 1 sorted, 2 as P.sorted_front says (one kernel serving both).
+template <class Rows, int G, int CPL, int Mode>
 __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int tier, int lane) {
     // seeds and exploration vertices come in caller ids (routed seeds in internal ids); rows are
     // read by internal id, keys carry the caller id
@@ -917,7 +918,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
     const int dim16 = (P.dim + 15) / 16 * 16;                  // zero padded to whole 16-element chunks
     for (int i = lane; i < dim16; i += 32) qv_smem[i] = i < P.dim ? qsrc[i] : 0.f;
     W.fn = W.back_n = W.res_n = 0;
-    W.sorted = P.sorted_front != 0;
+    const bool sorted = Mode == 2 ? P.sorted_front != 0 : Mode == 1;
+    W.sorted = sorted;
     W.wmark = kEmptyKey;
     W.trimmed = false;
     W.r2 = __int_as_float(0x7f800000);
@@ -972,7 +974,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             __syncwarp();
             const uint64_t k2 = make_key(W.cd2[0], s2c);
             if (lane == 0) {                                  // a sorted front stays descending
-                if (!W.sorted || k2 < W.front[0]) W.front[1] = k2;
+                if (!sorted || k2 < W.front[0]) W.front[1] = k2;
                 else { W.front[1] = W.front[0]; W.front[0] = k2; }
             }
             W.fn = 2;
@@ -996,12 +998,12 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         }
         // 1. pop the minimum of S (the front's minimum: its last key when sorted)
         uint64_t m;
-        const int mi = W.sorted ? W.fn - 1 : front_extreme(W, false, &m, lane);
-        if (W.sorted) m = W.front[mi];
+        const int mi = sorted ? W.fn - 1 : front_extreme(W, false, &m, lane);
+        if (sorted) m = W.front[mi];
         if (!thr.admits(key_d2(m))) break;                     // too far: return R
         if (P.max_hops && W.hops >= P.max_hops) { status = DEG_EHOPLIMIT; break; }
         __syncwarp();
-        if (lane == 0 && !W.sorted) W.front[mi] = W.front[W.fn - 1];
+        if (lane == 0 && !sorted) W.front[mi] = W.front[W.fn - 1];
         --W.fn;
         ++W.hops;
         const int32_t s = key_id(m);                           // caller id: the adjacency row
@@ -1063,7 +1065,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
             if (toS)  // its adjacency row is read if it is ever expanded: start pulling it into L2
                 asm volatile("prefetch.global.L2 [%0];" ::"l"(P.adj + (int64_t)id * P.deg_pad));
             adm += __popc(__ballot_sync(0xffffffffu, toS));
-            if (!(W.sorted ? admit_batch_sorted(W, make_key(d2, id), toS, thr_post, lane)
+            if (!(sorted ? admit_batch_sorted(W, make_key(d2, id), toS, thr_post, lane)
                            : admit_batch(W, make_key(d2, id), toS, thr_post, lane)))
                 return false;
         }
@@ -1118,7 +1120,7 @@ __device__ __forceinline__ uint8_t* load_stop_weights(Params& P, uint8_t* smem) 
     return smem + stop_bytes(1);
 }
 
-template <class Rows, int G, int CPL>
+template <class Rows, int G, int CPL, int Mode>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast_kernel(Params P) {
     extern __shared__ __align__(16) uint8_t smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1140,7 +1142,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) search_fast
         }
         q = __shfl_sync(0xffffffffu, q, 0);
         if (q >= P.nq) break;
-        const bool done = run_query<Rows, G, CPL>(P, W, q, qv, 0, lane);
+        const bool done = run_query<Rows, G, CPL, Mode>(P, W, q, qv, 0, lane);
         clear_visited(W, P, lane);
         if (!done && lane == 0) P.overflow[atomicAdd(P.counters, 1)] = q;
         __syncwarp();
@@ -1167,7 +1169,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) search_device_kernel(Para
         if (lane == 0) t = atomicAdd(P.counters + 1, 1);
         t = __shfl_sync(0xffffffffu, t, 0);
         if (t >= count) break;
-        run_query<Rows, G, CPL>(P, W, P.overflow[t], qv, 1, lane);
+        run_query<Rows, G, CPL, 1>(P, W, P.overflow[t], qv, 1, lane);   // queries with a large S: sorted front
         __syncwarp();
     }
 }
@@ -1298,7 +1300,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
                 Q.seeds_internal = 1;
             }
         }
-        const bool done = run_query<Rows, G, CPL>(Q, W, 0, qv, 0, lane);
+        const bool done = run_query<Rows, G, CPL, 2>(Q, W, 0, qv, 0, lane);
         clear_visited(W, Q, lane);
         if (!done) {
             for (int j = lane; j < m.x; j += 32) { Q.ids[j] = -1; Q.dists[j] = __int_as_float(0x7f800000); }
@@ -1360,7 +1362,7 @@ int launch_typed(Params P, cudaStream_t st, void* timer_start, void* timer_end, 
     const int wpb = (int)std::min<int64_t>(kWarpsPerBlock, (smem_max - sb) / wb);
     P.wpb = wpb;
     const int64_t smem = sb + wb * wpb;
-    auto fk = search_fast_kernel<Rows, G, CPL>;
+    auto fk = P.sorted_front ? search_fast_kernel<Rows, G, CPL, 1> : search_fast_kernel<Rows, G, CPL, 0>;
     if ((e = cudaFuncSetAttribute(fk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
         return *why = std::string("shared memory attribute: ") + cudaGetErrorString(e), (int)e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fk, wpb * 32, (size_t)smem)) != cudaSuccess)

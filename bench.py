@@ -12,6 +12,7 @@ sample of the same queries, at the same eps, and reported in the same format.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -272,7 +273,13 @@ def read_adjacency(path):
 
 def workload(args):
     w = synth.WORKLOADS[getattr(args, "workload", WORKLOAD)]
-    return synth.scaled(w, args.n, w.nq) if args.n else w
+    w = synth.scaled(w, args.n, w.nq) if args.n else w
+    d = getattr(args, "degree", 0)
+    if d:
+        # another even degree with the same Table 2 row otherwise (k_ext = 2d, k_opt = d, as the
+        # SIFT1M row has for d = 30), under its own name so its graph file is its own
+        w = dataclasses.replace(w, name=f"{w.name}-d{d}", degree=d, k_ext=2 * d, k_opt=d)
+    return w
 
 
 def run_reference(args, rank):
@@ -571,6 +578,7 @@ def main():
     ap.add_argument("--only", default=None, choices=["plain", "fp8-pivot", "fp8-learned", "bf16-learned"],
                     help="run one form at --eps for --warmup + --steps batches and nothing else (for profilers)")
     ap.add_argument("--train-queries", type=int, default=100_000, help="held-out queries traced for the stop network")
+    ap.add_argument("--degree", type=int, default=0, help="build and search the workload's graph at this even degree")
     ap.add_argument("--builder", default="host", choices=["host", "device"],
                     help="graph builder when the workload's graph file is missing")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")

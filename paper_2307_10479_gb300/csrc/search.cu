@@ -106,12 +106,14 @@ int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::
         P.order = ws.route + 3 * ws.cap_q;
         P.seeds_internal = 1;
     }
-    // walks from the fixed entry vertex run ~1,500 hops with a large S: keep its front sorted
-    P.sorted_front = (!P.seeds && !P.explore) ? 1 : 0;
     P.nq = (int32_t)a.nq;
     P.k = a.k;
     const bool reduced = a.precision != DEG_F32;
     P.ks = reduced && a.rerank > 0 ? std::max(a.rerank, a.k) : a.k;
+    // long walks keep the front of S sorted: from the fixed entry vertex (~1,500 hops), or with
+    // many results kept or a wide eps (hundreds of pops); short routed, seeded and exploration
+    // walks keep it unsorted
+    P.sorted_front = sorted_front_for(!P.seeds && !P.explore, P.ks, a.eps) ? 1 : 0;
     P.kcap = std::max(32, pow2_at_least(P.ks));
     P.rerank = reduced && a.rerank >= 0 ? 1 : 0;             // -1: the reduced-precision distances as computed
     const float2 fe = eps_factor(a.eps);

@@ -904,6 +904,14 @@ inline __device__ void clear_visited(WarpState& W, const Params& P, int lane) {
     __syncwarp();
 }
 
+// Which front a query's S keeps: sorted for long walks (from the fixed entry vertex, or with 64 or
+// more results kept, or eps of 0.02 or more: hundreds to thousands of pops), unsorted for short
+// ones (measured on the 1M x 128 workload: the unsorted front is 6% faster for the 34-hop routed
+// walks and 6-13% slower for the long ones).
+__host__ __device__ inline bool sorted_front_for(bool fixed_entry, int ks, float eps) {
+    return fixed_entry || ks >= 64 || eps >= 0.02f;
+}
+
 // Mode: 0 the front of S unsorted, 1 sorted, 2 as P.sorted_front says (one kernel serving both).
 template <class Rows, int G, int CPL, int Mode>
 __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, int tier, int lane) {
@@ -1281,7 +1289,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32, kBlocksPerSM) serve_kerne
         Q.status = S.status + r;
         Q.trace = S.trace + 4 * (int64_t)r;
         Q.seeds_internal = 0;
-        Q.sorted_front = (m.z < 0 && S.entry_mode == 0) ? 1 : 0;
+        Q.sorted_front = sorted_front_for(m.z < 0 && S.entry_mode == 0, Q.ks, __int_as_float(m.y)) ? 1 : 0;
         if (m.z >= 0) {                                       // exploration from vertex m.z
             Q.explore = 1;
             Q.seeds = reinterpret_cast<const int32_t*>(S.meta + r) + 2;

@@ -65,7 +65,7 @@ def test_plain_float32_form_matches_the_oracle_exactly(full):
 
 def test_headline_fp8_form_against_the_oracle(full):
     idx, base, adj, qs, gt = full["idx"], full["base"], full["adj"], full["qs"], full["gt"]
-    eps = 0.003                                       # the headline's operating point (recall 0.950)
+    eps = 0.003                                       # the sampled-pivot fp8 form's operating point (recall 0.950)
     ids, d, st = idx.search(full["qd"], k=10, eps=eps, precision="fp8", rerank=32, entry="pivot",
                             with_status=True)
     torch.cuda.synchronize()
@@ -85,5 +85,28 @@ def test_headline_fp8_form_against_the_oracle(full):
     assert abs(recall(ids, gt) - recall(o_ids, gt)) <= 0.01
     np.testing.assert_allclose(d[same], o_d[same], rtol=1e-5)
     # re-ranked: the returned distances are the float32 rows' distances of the returned ids
+    true = np.sqrt(((base[ids].astype(np.float64) - qs[:, None, :]) ** 2).sum(-1))
+    np.testing.assert_allclose(d, true, rtol=1e-5)
+
+
+def test_headline_fp8_learned_entry_form_against_the_oracle(full):
+    # the bench's headline: fp8 + re-rank 32 from the learned entry points, eps 0.001; the oracle
+    # starts each sampled query at the nearest learned entry point (FP64 brute force over them)
+    idx, base, adj, qs, gt = full["idx"], full["base"], full["adj"], full["qs"], full["gt"]
+    idx.train_entry(len(idx.pivots()), 10)
+    piv = idx.pivots(learned=True)
+    eps = 0.001
+    ids, d, st = idx.search(full["qd"], k=10, eps=eps, precision="fp8", rerank=32, entry="learned", with_status=True)
+    torch.cuda.synchronize()
+    ids, d, st = ids.cpu().numpy()[SAMPLE], d.cpu().numpy()[SAMPLE], st.cpu().numpy()
+    assert (st == 0).all()
+    lab, _ = oracle.knn_bruteforce(base[piv], qs, 1)
+    codes, scales = oracle.quantize_fp8(base)
+    dec = oracle.decode("fp8", codes, scales)
+    o_ids, o_d = oracle.range_search_decoded(dec, base, adj, qs, piv[lab[:, 0]], 10, eps32(eps), keep=32)
+    del dec
+    same = np.all(ids == o_ids, axis=1)
+    assert same.mean() >= 0.95, f"{same.mean():.3f} of the sampled lists identical"
+    assert abs(recall(ids, gt) - recall(o_ids, gt)) <= 0.01
     true = np.sqrt(((base[ids].astype(np.float64) - qs[:, None, :]) ** 2).sum(-1))
     np.testing.assert_allclose(d, true, rtol=1e-5)

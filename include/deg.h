@@ -128,6 +128,19 @@ DEG_API deg_status deg_insert_device(deg_index* idx, const float* new_host, int6
  * the device copy released: upload again before searching. p->degree must equal the index's. */
 DEG_API deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
 
+/* Remove vertex v (0 <= v < n) from the index on the host. The paper leaves removal open (App. A)
+ * while calling the graph fully dynamic; this removal keeps every invariant. v's d edges go; its
+ * former neighbours, each one edge short, are joined in pairs by new edges, closest non-adjacent
+ * pairs first (ties by ids); a pair left that is already adjacent is joined through a nearby edge
+ * (x, y), replaced by (a, x) and (b, y), x a neighbour of a neighbour of a, minimising
+ * |a-x| + |b-y| - |x-y|. The graph stays connected exactly when the former neighbours still reach
+ * one another, which is checked. Then the last vertex n-1 takes id v (its vector and edges move;
+ * *moved_from (nullable) = n-1, or -1 if v was n-1) and n shrinks by one, so ids stay 0 .. n-2.
+ * The device copy is released (upload again before searching). DEG_EINVAL (index unchanged) if v
+ * is out of range, if fewer than degree + 1 vertices would remain, or if no reconnection keeps the graph
+ * connected; DEG_EGRAPH if the result violates an invariant. */
+DEG_API deg_status deg_remove(deg_index* idx, int32_t v, int32_t* moved_from);
+
 /* Wrap an existing graph: base_host [n][dim] float32 and adj_host [n][degree] int32 are copied.
  * The adjacency is checked (every entry in [0,n), no self-loops, no duplicates, symmetric,
  * degree even and >= 4): DEG_EGRAPH if it is not a valid undirected regular graph. */

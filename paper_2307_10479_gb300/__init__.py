@@ -72,6 +72,7 @@ def lib() -> ctypes.CDLL:
             "deg_build_device": (S, [P, i64, i32, ctypes.POINTER(BuildParams), i32, P, ctypes.POINTER(P), P]),
             "deg_refine_device": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_insert_device": (S, [P, P, i64, ctypes.POINTER(BuildParams), i32, P]),
+            "deg_remove": (S, [P, i32, ctypes.POINTER(i32)]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -179,6 +180,12 @@ class Index:
         p = BuildParams(degree, k_ext, eps_ext, k_opt or degree, eps_opt, i_opt, 0, 0)
         _check(lib().deg_insert_device(self._h, vectors.ctypes.data, vectors.shape[0], ctypes.byref(p), batch_div,
                                        _stream_ptr(stream)))
+
+    def remove(self, v: int) -> int:
+        """Remove vertex v (deg_remove); the last vertex takes id v. Returns its old id, or -1 if v was last."""
+        moved = ctypes.c_int32(-1)
+        _check(lib().deg_remove(self._h, int(v), ctypes.byref(moved)))
+        return moved.value
 
     def refine_device(self, rounds: int, k_opt: int, eps_opt: float, i_opt: int, seed: int = 0, stream=None) -> int:
         """Alg. 5 for `rounds` random vertices on the GPU (deg_refine_device); returns the improved count."""

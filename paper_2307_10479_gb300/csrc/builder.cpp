@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstring>
 #include <queue>
+#include <unordered_set>
 #include <stdexcept>
 #include <vector>
 
@@ -320,6 +321,166 @@ int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& 
     }
     if (progress) *progress = n;
     std::memcpy(adj_out, g.nb_.data(), sizeof(int32_t) * (size_t)n * p.degree);
+    return 0;
+}
+
+}  // namespace deg
+
+// ---- removing a vertex (not in the paper) -----------------------------------------------------
+// The paper builds and refines the graph but leaves removal open. A removal that keeps every
+// invariant: drop v's d edges; its former neighbours, each one edge short, are paired by new
+// edges (closest non-adjacent pairs first); a pair left adjacent is joined through a nearby edge
+// (x, y), replaced by (a, x) and (b, y). If all former neighbours reach each other afterwards, the
+// graph is connected (every vertex reached v through one of them); otherwise every change is
+// undone and the removal refused. Finally the last vertex takes v's id, so ids stay 0 .. n-2.
+// Work per removal: O(d^3) distances for the reconnection and a search that ends once the former
+// neighbours have met (a few hops in a DEG), so removals cost the same on any graph size.
+namespace deg {
+namespace {
+
+float dist_rows(const float* x, int dim, int32_t a, int32_t b) {
+    double s = 0.0;
+    for (int i = 0; i < dim; ++i) {
+        const double t = (double)x[(size_t)a * dim + i] - (double)x[(size_t)b * dim + i];
+        s += t * t;
+    }
+    return (float)std::sqrt(s);
+}
+
+}  // namespace
+
+int remove_vertex(std::vector<float>& x, std::vector<int32_t>& adj, int64_t& n, int32_t dim, int32_t d, int32_t v,
+                  int32_t* moved_from, std::vector<int32_t>* touched, std::string* why) {
+    if (v < 0 || v >= n) return *why = "vertex out of range", 1;
+    if (n <= d + 1) return *why = "the graph would have fewer than degree + 1 vertices", 1;
+    auto row = [&](int32_t u) { return adj.data() + (size_t)u * d; };
+    auto slot = [&](int32_t a, int32_t b) {
+        const int32_t* r = row(a);
+        for (int j = 0; j < d; ++j)
+            if (r[j] == b) return j;
+        return -1;
+    };
+    auto linked = [&](int32_t a, int32_t b) { return slot(a, b) >= 0; };
+    std::vector<std::pair<size_t, int32_t>> undo;                 // (adjacency slot, old value)
+    auto set = [&](int32_t a, int j, int32_t value) {
+        undo.emplace_back((size_t)a * d + j, row(a)[j]);
+        row(a)[j] = value;
+    };
+    auto rollback = [&] {
+        for (size_t i = undo.size(); i-- > 0;) adj[undo[i].first] = undo[i].second;
+    };
+    auto link = [&](int32_t a, int32_t b) {
+        set(a, slot(a, -1), b);
+        set(b, slot(b, -1), a);
+    };
+    auto unlink = [&](int32_t a, int32_t b) {
+        set(a, slot(a, b), -1);
+        set(b, slot(b, a), -1);
+    };
+    const std::vector<int32_t> nb(row(v), row(v) + d);
+    for (int32_t u : nb) unlink(v, u);                            // each neighbour: one free slot
+    // closest non-adjacent pairs first (ties by the pair's slots in v's row)
+    struct Pair {
+        float w;
+        int i, j;
+    };
+    std::vector<Pair> pairs;
+    for (int i = 0; i < d; ++i)
+        for (int j = i + 1; j < d; ++j)
+            if (!linked(nb[i], nb[j])) pairs.push_back({dist_rows(x.data(), dim, nb[i], nb[j]), i, j});
+    std::sort(pairs.begin(), pairs.end(), [&](const Pair& p, const Pair& q) {
+        if (p.w != q.w) return p.w < q.w;
+        if (nb[p.i] != nb[q.i]) return nb[p.i] < nb[q.i];
+        return nb[p.j] < nb[q.j];
+    });
+    std::vector<char> done(d, 0);
+    for (const Pair& p : pairs) {
+        if (done[p.i] || done[p.j]) continue;
+        link(nb[p.i], nb[p.j]);
+        done[p.i] = done[p.j] = 1;
+    }
+    // the rest, two at a time (each pair adjacent): replace a nearby edge (x, y) by (a, x), (b, y),
+    // x a neighbour of a neighbour of a, minimising |a-x| + |b-y| - |x-y|
+    std::vector<int32_t> left;
+    for (int i = 0; i < d; ++i)
+        if (!done[i]) left.push_back(nb[i]);
+    for (size_t i = 0; i + 1 < left.size(); i += 2) {
+        const int32_t a = left[i], b = left[i + 1];
+        float best = INFINITY;
+        int32_t bx = -1, by = -1;
+        for (int j = 0; j < d; ++j) {
+            const int32_t m = row(a)[j];
+            if (m < 0) continue;
+            for (int jj = 0; jj < d; ++jj) {
+                const int32_t xx = row(m)[jj];
+                if (xx < 0 || xx == a || xx == b || linked(a, xx)) continue;
+                const float ax = dist_rows(x.data(), dim, a, xx);
+                for (int k = 0; k < d; ++k) {
+                    const int32_t yy = row(xx)[k];
+                    if (yy < 0 || yy == a || yy == b || linked(b, yy)) continue;
+                    const float c = ax + dist_rows(x.data(), dim, b, yy) - dist_rows(x.data(), dim, xx, yy);
+                    if (c < best) {
+                        best = c;
+                        bx = xx;
+                        by = yy;
+                    }
+                }
+            }
+        }
+        if (bx < 0) {
+            rollback();
+            return *why = "no edge to reconnect the removed vertex's neighbours", 1;
+        }
+        unlink(bx, by);
+        link(a, bx);
+        link(b, by);
+    }
+    // connected iff the former neighbours reach each other; the search stops once all have met
+    {
+        std::vector<int32_t> queue{nb[0]};
+        std::unordered_set<int32_t> seen{nb[0]};
+        const std::unordered_set<int32_t> want(nb.begin(), nb.end());
+        int found = 1;
+        for (size_t h = 0; h < queue.size() && found < d; ++h) {
+            const int32_t* r = row(queue[h]);
+            for (int j = 0; j < d; ++j) {
+                const int32_t w = r[j];
+                if (w < 0 || !seen.insert(w).second) continue;
+                found += (int)want.count(w);
+                queue.push_back(w);
+            }
+        }
+        if (found < d) {
+            rollback();
+            return *why = "removing this vertex would disconnect the graph", 1;
+        }
+    }
+    // the last vertex takes v's id
+    const int32_t last = (int32_t)(n - 1);
+    if (moved_from) *moved_from = v == last ? -1 : last;
+    if (v != last) {
+        for (int j = 0; j < d; ++j) {
+            const int32_t u = row(last)[j];
+            row(u)[slot(u, last)] = v;
+            row(v)[j] = u;
+        }
+        std::copy(x.begin() + (size_t)last * dim, x.begin() + (size_t)(last + 1) * dim, x.begin() + (size_t)v * dim);
+    }
+    if (touched) {
+        touched->clear();
+        for (const auto& e : undo) {
+            const int32_t u = (int32_t)(e.first / d);
+            touched->push_back(u == last ? v : u);
+        }
+        if (v != last)
+            for (int j = 0; j < d; ++j) touched->push_back(row(v)[j]);
+        std::sort(touched->begin(), touched->end());
+        touched->erase(std::unique(touched->begin(), touched->end()), touched->end());
+        if (v == last) touched->erase(std::remove(touched->begin(), touched->end(), v), touched->end());
+    }
+    --n;
+    adj.resize((size_t)n * d);
+    x.resize((size_t)n * dim);
     return 0;
 }
 

@@ -83,6 +83,25 @@ deg_status check_graph(const int32_t* adj, int64_t n, int32_t d) {
     return DEG_OK;
 }
 
+// check_graph over the rows of the vertices `rows` only (a local edit keeps the rest as it was).
+deg_status check_rows(const int32_t* adj, int64_t n, int32_t d, const std::vector<int32_t>& rows) {
+    for (const int32_t u : rows) {
+        const int32_t* r = adj + (int64_t)u * d;
+        for (int32_t j = 0; j < d; ++j) {
+            const int32_t v = r[j];
+            if (v < 0 || v >= n) return fail(DEG_EGRAPH, "neighbour id out of range at vertex " + std::to_string(u));
+            if (v == u) return fail(DEG_EGRAPH, "self loop at vertex " + std::to_string(u));
+            for (int32_t i = 0; i < j; ++i)
+                if (r[i] == v) return fail(DEG_EGRAPH, "duplicate edge at vertex " + std::to_string(u));
+            const int32_t* b = adj + (int64_t)v * d;
+            bool back = false;
+            for (int32_t i = 0; i < d && !back; ++i) back = (b[i] == u);
+            if (!back) return fail(DEG_EGRAPH, "asymmetric edge " + std::to_string(u) + "-" + std::to_string(v));
+        }
+    }
+    return DEG_OK;
+}
+
 void free_device(deg_index* idx) {
     DeviceIndex& d = idx->dev;
     cudaFree(d.x32);
@@ -245,6 +264,19 @@ extern "C" deg_status deg_refine_device(deg_index* idx, const deg_build_params* 
     if (s != DEG_OK) return s;
     free_device(idx);                                          // the device copy shows the old graph
     return DEG_OK;
+}
+
+extern "C" deg_status deg_remove(deg_index* idx, int32_t v, int32_t* moved_from) {
+    if (!idx) return fail(DEG_EINVAL, "deg_remove: NULL index");
+    if (v < 0 || v >= idx->n) return fail(DEG_EINVAL, "deg_remove: vertex out of range");
+    std::string why;
+    int32_t moved = -1;
+    std::vector<int32_t> touched;
+    if (deg::remove_vertex(idx->x, idx->adj, idx->n, idx->dim, idx->degree, v, &moved, &touched, &why) != 0)
+        return fail(DEG_EINVAL, "deg_remove: " + why);
+    if (moved_from) *moved_from = moved;
+    free_device(idx);                                          // the device copy shows the old graph
+    return check_rows(idx->adj.data(), idx->n, idx->degree, touched);
 }
 
 extern "C" deg_status deg_index_from_arrays(const float* base_host, const int32_t* adj_host, int64_t n,

@@ -20,6 +20,14 @@ constexpr int kStopParams = 5122;   // 12*64 + 64 + 64*64 + 64 + 2*64 + 2
 int build_graph(const float* x, int64_t n, int32_t dim, const deg_build_params& p, int32_t* adj_out,
                 volatile int64_t* progress);
 
+// Removes vertex v from the graph adj [n][d] over rows x [n][dim] (builder.cpp): its neighbours are
+// re-paired so the graph stays even-regular, symmetric and connected, then the last vertex takes
+// id v (*moved_from = n-1, or -1 when v was last) and n shrinks by one; *touched (nullable) gets
+// the ids, after the move, of every vertex whose row changed. Returns 0, or 1 with *why set and
+// nothing changed.
+int remove_vertex(std::vector<float>& x, std::vector<int32_t>& adj, int64_t& n, int32_t dim, int32_t d, int32_t v,
+                  int32_t* moved_from, std::vector<int32_t>* touched, std::string* why);
+
 // Device construction (build_gpu.cu): batched ExtendGraph on the current device, adjacency
 // [n][degree] written to adj_out (host). Returns a cudaError_t value (0 = success).
 int build_graph_device(const float* x_host, int64_t n, int32_t dim, const deg_build_params& p, int32_t batch_div,

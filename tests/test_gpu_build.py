@@ -134,3 +134,42 @@ def test_insert_grows_a_graph_like_a_build():
     assert np.mean(ids.cpu().numpy()[:, 0] == np.arange(6000, 6100)) >= 0.99   # new rows find themselves
     with pytest.raises(deg.DegError):
         idx.insert_device(base[:10], 4, 0.2)                 # k_ext below the degree
+
+
+def test_removal_then_insertion_keeps_search_quality():
+    # 8,000 rows built on the device; 2,000 random vertices removed (deg_remove, each re-pairing its
+    # neighbours and moving the last vertex into its id); the graph keeps its invariants, Alg. 1 on
+    # it reaches the recall of a fresh build over the 6,000 rows left, the library's search on it is
+    # the oracle's; the removed rows inserted again find themselves
+    import paper_2307_10479_gb300 as deg
+    w = synth.scaled(synth.WORKLOADS["sift-1m-d128"], 8_000, 200)
+    base, q = w.base(), w.queries()
+    idx = deg.Index.build_device(base, 30, 60, 0.2, k_opt=30, i_opt=5)
+    rows = np.arange(8000)                         # id -> row of base
+    rng = np.random.default_rng(11)
+    for _ in range(2000):
+        v = int(rng.integers(len(rows)))
+        moved = idx.remove(v)
+        if moved >= 0:
+            rows[v] = rows[moved]
+        rows = rows[:-1]
+    n, _, degree = idx.info()
+    adj = idx.adjacency()
+    assert (n, degree) == (6000, 30) and oracle.check_graph(adj) == 0
+    left = base[rows]
+    fresh = deg.Index.build_device(left, 30, 60, 0.2, k_opt=30, i_opt=5).adjacency()
+    gt, _ = oracle.knn_bruteforce(left, q, 10)
+    entry = np.full(len(q), oracle.median_vertex(left), np.int32)
+    r_rem = recall(oracle.range_search(left, adj, q, entry, 10, 0.1)[0], gt)
+    r_new = recall(oracle.range_search(left, fresh, q, entry, 10, 0.1)[0], gt)
+    assert r_rem >= r_new - 0.02, (r_rem, r_new)
+    idx.upload()
+    ids, d = idx.search(torch.from_numpy(q).cuda(), k=10, eps=0.1)
+    o_ids, o_d, _ = oracle.range_search(left, adj, q, entry, 10, eps32(0.1))
+    compare_lists(ids.cpu().numpy(), d.cpu().numpy(), o_ids, o_d)
+    gone = np.setdiff1d(np.arange(8000), rows)
+    idx.insert_device(base[gone], 60, 0.2, k_opt=30, i_opt=5)
+    assert idx.info()[0] == 8000 and oracle.check_graph(idx.adjacency()) == 0
+    idx.upload()
+    ids, _ = idx.search(torch.from_numpy(base[gone[:100]]).cuda(), k=1, eps=0.1)
+    assert np.mean(ids.cpu().numpy()[:, 0] == np.arange(6000, 6100)) >= 0.99

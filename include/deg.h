@@ -128,6 +128,25 @@ DEG_API deg_status deg_insert_device(deg_index* idx, const float* new_host, int6
  * the device copy released: upload again before searching. p->degree must equal the index's. */
 DEG_API deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
 
+/* Alg. 5 (Sec. 5.3: continuous refinement) as deg_refine_device, on an UPLOADED index that stays in
+ * use: a serving kernel (deg_serve_start) may run throughout. The refinement runs on a copy of the
+ * graph; after each batch of up to 4,096 rounds (all their optimisations finished or reverted, so
+ * the copy is a valid DEG again) the entries of the device adjacency that changed are rewritten in
+ * place, each with one 64-bit store that the serving kernel reads with one 64-bit load at GPU
+ * scope. A request served meanwhile walks a mix of the old and new graph: every neighbour it reads
+ * is a vertex, so its results are vertices with their exact distances, but which vertices it finds
+ * may differ from a search on either graph alone. The serving kernel must leave the GPU room for
+ * the refinement's kernels (deg_serve_config.max_blocks), or they run only once it ends. On return
+ * the device adjacency equals the host adjacency, which holds the refined graph (checked; the
+ * device copy is kept). Batched searches (deg_search*) must not run during the call: they read the
+ * adjacency through the read-only cache. Device memory of the call (about the float32 rows and two
+ * adjacency copies) is allocated and freed stream-ordered on `stream` (NULL: a stream of its own),
+ * so nothing in it waits for the serving kernel. DEG_ENOTREADY if the index is not uploaded;
+ * DEG_EINVAL / DEG_ECUDA / DEG_EGRAPH as deg_refine_device. On an error the host adjacency takes
+ * the device copy's graph (the batches published before it), so the two stay equal; if that copy
+ * fails too, the device copy is released (upload again). */
+DEG_API deg_status deg_refine_live(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
+
 /* Remove vertex v (0 <= v < n) from the index on the host. The paper leaves removal open (App. A)
  * while calling the graph fully dynamic; this removal keeps every invariant. v's d edges go; its
  * former neighbours, each one edge short, are joined in pairs by new edges, closest non-adjacent
@@ -314,6 +333,8 @@ typedef struct {
                                 learned entry point                                               */
     int32_t learned_stop;    /* 1: use the index's stop network                                    */
     double idle_timeout_s;   /* end the kernel when no request arrives for this long (> 0)         */
+    int32_t max_blocks;      /* 0: as many blocks of 8 warps as fit on the GPU; else at most this
+                                many, leaving the rest to other kernels (deg_refine_live)          */
 } deg_serve_config;
 
 /* Launch the serving kernel on its own stream. The index must stay alive until deg_serve_stop. */

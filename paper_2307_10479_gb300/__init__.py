@@ -49,7 +49,7 @@ class SearchParams(ctypes.Structure):
 class ServeConfig(ctypes.Structure):
     _fields_ = [("capacity", ctypes.c_int32), ("kmax", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("rerank", ctypes.c_int32), ("entry_mode", ctypes.c_int32), ("learned_stop", ctypes.c_int32),
-                ("idle_timeout_s", ctypes.c_double)]
+                ("idle_timeout_s", ctypes.c_double), ("max_blocks", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -73,6 +73,7 @@ def lib() -> ctypes.CDLL:
             "deg_refine_device": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_insert_device": (S, [P, P, i64, ctypes.POINTER(BuildParams), i32, P]),
             "deg_remove": (S, [P, i32, ctypes.POINTER(i32)]),
+            "deg_refine_live": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -180,6 +181,16 @@ class Index:
         p = BuildParams(degree, k_ext, eps_ext, k_opt or degree, eps_opt, i_opt, 0, 0)
         _check(lib().deg_insert_device(self._h, vectors.ctypes.data, vectors.shape[0], ctypes.byref(p), batch_div,
                                        _stream_ptr(stream)))
+
+    def refine_live(self, rounds: int, k_opt: int, eps_opt: float, i_opt: int, seed: int = 0, stream=None) -> int:
+        """Alg. 5 on the uploaded index while a Server may be running (deg_refine_live); returns the
+        improved count. The device copy is updated in place batch by batch and kept."""
+        _, _, degree = self.info()
+        p = BuildParams(degree, degree, 0.2, k_opt, eps_opt, i_opt, rounds, seed)
+        improved = ctypes.c_int64()
+        _check(lib().deg_refine_live(self._h, ctypes.byref(p), ctypes.byref(improved),
+                                     None if stream is None else _stream_ptr(stream)))
+        return improved.value
 
     def remove(self, v: int) -> int:
         """Remove vertex v (deg_remove); the last vertex takes id v. Returns its old id, or -1 if v was last."""
@@ -346,12 +357,13 @@ class Server:
     """Continuous-batching server: a persistent kernel serving requests posted to a ring."""
 
     def __init__(self, index: "Index", capacity: int = 65536, kmax: int = 128, precision: str = "f32",
-                 rerank: int = 0, entry: str = "fixed", learned_stop: bool = False, idle_timeout_s: float = 30.0):
+                 rerank: int = 0, entry: str = "fixed", learned_stop: bool = False, idle_timeout_s: float = 30.0,
+                 max_blocks: int = 0):
         self.index = index
         self.kmax = kmax
         self.dim = index.info()[1]
         cfg = ServeConfig(capacity, kmax, PRECISIONS[precision], rerank, ENTRY_MODES[entry],
-                          1 if learned_stop else 0, float(idle_timeout_s))
+                          1 if learned_stop else 0, float(idle_timeout_s), int(max_blocks))
         self._h = ctypes.c_void_p()
         _check(lib().deg_serve_start(index._h, ctypes.byref(cfg), ctypes.byref(self._h)))
 

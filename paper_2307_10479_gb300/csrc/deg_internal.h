@@ -41,6 +41,14 @@ int insert_vertices_device(const float* x_host, int32_t* adj, int64_t n_old, int
 int refine_graph_device(const float* x_host, const int32_t* adj_in, int64_t n, int32_t dim, const deg_build_params& p,
                         int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why);
 
+struct DeviceIndex;
+// Alg. 5 as refine_graph_device, while the uploaded index ix stays in use by a serving kernel: after
+// each batch of rounds the entries of ix.adj that changed are rewritten in place, one 64-bit
+// relaxed store each. Every device allocation of the run is stream-ordered on `stream`, so nothing
+// waits for the serving kernel. adj_out gets the final graph.
+int refine_graph_live(const float* x_host, const int32_t* adj_in, DeviceIndex& ix, const deg_build_params& p,
+                      int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why);
+
 // Record an error message for deg_last_error() and return the status.
 deg_status fail(deg_status s, const std::string& msg);
 
@@ -95,6 +103,10 @@ struct Workspace {
     uint32_t* pbitmaps = nullptr;    // second kernel: [pslots][words]
     uint64_t* pbacks = nullptr;      //   [pslots][n + 1]
     int32_t pslots = 0;
+    // stream-ordered allocation (cudaMallocAsync / cudaFreeAsync on this stream): no allocation or
+    // free of this workspace waits for other streams' kernels (a persistent serving kernel)
+    bool stream_ordered = false;
+    void* alloc_stream = nullptr;
     // host e2e staging
     void* dq = nullptr;
     void* did = nullptr;
@@ -147,6 +159,7 @@ struct ServeArgs {
     unsigned long long* claim;
     int32_t cap, kmax, entry_mode, precision, rerank, learned_stop;
     unsigned long long idle_ns;
+    int32_t max_blocks;       // 0: as many resident blocks as fit
 };
 
 // Kernel launchers (search.cu). Return a cudaError_t value (0 = success).

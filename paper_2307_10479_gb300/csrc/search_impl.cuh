@@ -367,6 +367,15 @@ inline __device__ float exact_d2_lane(const float* x32, int32_t dim_pad, int32_t
     return a;
 }
 
+// One adjacency entry {internal id, caller id} as a single 64-bit relaxed load at GPU scope: the
+// serving kernel runs while deg_refine_live rewrites rows, so an entry must never be half old and
+// half new, and a row must not be served from a stale L1 line for the life of the kernel.
+__device__ __forceinline__ int2 load_adj_live(const int2* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
+    return make_int2((int32_t)(uint32_t)(v & 0xffffffffull), (int32_t)(uint32_t)(v >> 32));
+}
+
 // Test-and-set of vertex id in C: 1 if it was not checked yet.
 __device__ __forceinline__ int visit(uint32_t* bm, int32_t id) {
     const uint32_t bit = 1u << (id & 31);
@@ -1021,7 +1030,8 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         int cnt = 0;
         for (int j0 = 0; j0 < P.degree; j0 += 32) {
             const int j = j0 + lane;
-            const int2 e = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : make_int2(-1, -1);
+            const int2* ep = P.adj + (int64_t)s * P.deg_pad + j;
+            const int2 e = j >= P.degree ? make_int2(-1, -1) : Mode == 2 ? load_adj_live(ep) : __ldg(ep);
             const int32_t nb = e.x;
             if (nb >= 0 && P.row_bytes <= DEG_SEARCH_ROW_PREFETCH_BYTES) {
                 // start pulling the row into L2 while the visited test is in flight (a visited
@@ -1204,6 +1214,7 @@ struct ServeRing {
     unsigned long long* claim;            // next request number (device memory)
     int32_t cap, kmax, entry_mode;
     unsigned long long idle_ns;
+    int32_t max_blocks;                   // 0: as many resident blocks as fit
 };
 
 __device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
@@ -1338,8 +1349,10 @@ int launch_serve(Params P, const ServeRing& S, const int32_t* pivots, int np, cu
         return *why = std::string("serve attribute: ") + cudaGetErrorString(e), (int)e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWarpsPerBlock * 32, (size_t)smem)) != cudaSuccess)
         return *why = "occupancy query failed", (int)e;
-    // every block must be resident at once (persistent); never more warps than device slots
-    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)P.slots / kWarpsPerBlock));
+    // every block must be resident at once (persistent); never more warps than device slots, nor
+    // more blocks than the caller allows (the rest of the GPU stays free for other work)
+    int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (int64_t)P.slots / kWarpsPerBlock));
+    if (S.max_blocks > 0) grid = std::min<int64_t>(grid, S.max_blocks);
     *warps = (int)(grid * kWarpsPerBlock);
     k<<<(unsigned)grid, kWarpsPerBlock * 32, smem, st>>>(P, S, pivots, np);
     if ((e = cudaGetLastError()) != cudaSuccess) return *why = std::string("serve kernel: ") + cudaGetErrorString(e), (int)e;

@@ -108,6 +108,17 @@ def test_search_before_upload_is_rejected(L):
     assert L.deg_upload(None, 1, None) == deg.DEG_EINVAL
 
 
+def test_live_refinement_needs_an_uploaded_index(L):
+    base = synth.uniform(100, 4, 46)
+    idx = deg.Index.build(base, 4, 8, 0.2, 4, 0.001, 0)
+    p = deg.BuildParams(4, 4, 0.2, 4, 0.001, 5, 10, 0)
+    assert L.deg_refine_live(idx._h, ctypes.byref(p), None, None) == deg.DEG_ENOTREADY
+    assert b"not uploaded" in L.deg_last_error()
+    assert L.deg_refine_live(None, ctypes.byref(p), None, None) == deg.DEG_EINVAL
+    # the serving configuration's layout: max_blocks follows idle_timeout_s
+    assert deg.ServeConfig.max_blocks.offset == 32 and ctypes.sizeof(deg.ServeConfig) == 40
+
+
 def test_knn_exact_argument_checks(L):
     assert L.knn_exact(None, 10, None, 1, 4, 1, None, None, None) == deg.DEG_EINVAL
     assert L.knn_exact(ctypes.c_void_p(16), 10, ctypes.c_void_p(16), 1, 4, 0, ctypes.c_void_p(16),

@@ -434,7 +434,11 @@ def serving(deg, idx, w, q, gt):
                                        "device_p50_ms": 1e3 * float(np.median(dev)),
                                        "device_p99_ms": 1e3 * float(np.percentile(dev, 99)),
                                        "rest_p50_ms": 1e3 * float(np.median(lat - dev)),
-                                       "rest_p99_ms": 1e3 * float(np.percentile(lat - dev, 99))}
+                                       "rest_p99_ms": 1e3 * float(np.percentile(lat - dev, 99)),
+                                       # the rate the slots sustain when every one is busy: slots over
+                                       # the mean device time of a request of this mix
+                                       "device_mean_ms": 1e3 * float(np.mean(dev)),
+                                       "slots_ceiling_qps": srv.slots / float(np.mean(dev))}
             log(f"[bench] serving {rate}/s: sustained {n / wall:.0f}/s, p50 {1e3 * np.median(lat):.2f} ms, "
                 f"p99 {1e3 * np.percentile(lat, 99):.2f} ms, recall@10 {rec:.4f}")
     finally:
@@ -444,8 +448,8 @@ def serving(deg, idx, w, q, gt):
 
 def serve_while_refining(deg, idx, w, q, gt, rate=200_000, seconds=3.0, chunk=32_768):
     """Continuous refinement (Alg. 5) on the device while the serving kernel answers requests on
-    the same index (deg_refine_live). The server keeps two blocks of 8 warps per SM and leaves the
-    third to the refinement. Measured: the same Poisson trace of k = 10 vector requests (eps 0.1,
+    the same index (deg_refine_live). The server keeps at most two blocks of 4 warps per SM and
+    leaves the rest of each SM to the refinement. Measured: the same Poisson trace of k = 10 vector requests (eps 0.1,
     bfloat16 rows, pivot entry) served alone and during refinement, and the refinement's rounds/s
     alone (no server) and while serving. Refinement runs in calls of `chunk` rounds, each a fresh
     copy of the graph on the device, so rounds/s includes that set-up."""
@@ -645,7 +649,7 @@ def main():
                     help="run one form at --eps for --warmup + --steps batches and nothing else (for profilers)")
     ap.add_argument("--train-queries", type=int, default=100_000, help="held-out queries traced for the stop network")
     ap.add_argument("--degree", type=int, default=0, help="build and search the workload's graph at this even degree")
-    ap.add_argument("--builder", default="host", choices=["host", "device"],
+    ap.add_argument("--builder", default="device", choices=["host", "device"],
                     help="graph builder when the workload's graph file is missing")
     ap.add_argument("--n", type=int, default=0, help="use the first n base rows (profiling only)")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(synth.WORKLOADS),
@@ -887,7 +891,11 @@ def main():
         line["cpu_baseline"] = cpu_baseline(base, idx.adjacency(), q, oracle.median_vertex(base), plain["eps"])
     if not args.no_serve and not args.no_refine_live:
         # last: it changes the graph the other measurements ran on
-        line["serving"]["while_refining"] = serve_while_refining(deg, idx, w, q, gt)
+        try:
+            line["serving"]["while_refining"] = serve_while_refining(deg, idx, w, q, gt)
+        except Exception as exc:                     # reported, not fatal to the measurements above
+            line["serving"]["while_refining"] = {"error": str(exc)}
+            log(f"[bench] serving while refining failed: {exc}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

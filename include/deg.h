@@ -140,8 +140,13 @@ DEG_API deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, 
  * the device adjacency equals the host adjacency, which holds the refined graph (checked; the
  * device copy is kept). Batched searches (deg_search*) must not run during the call: they read the
  * adjacency through the read-only cache. Device memory of the call (about the float32 rows and two
- * adjacency copies) is allocated and freed stream-ordered on `stream` (NULL: a stream of its own),
- * so nothing in it waits for the serving kernel. DEG_ENOTREADY if the index is not uploaded;
+ * adjacency copies, plus search scratch) is allocated and freed stream-ordered on `stream` (NULL: a
+ * stream of its own) from a memory pool of the library's own, which keeps the memory for the next
+ * call until the process exits, so that no allocation, free or synchronisation of the call waits for
+ * the serving kernel. deg_serve_start loads the refinement's kernels before it launches the serving
+ * kernel: under lazy module loading (the CUDA default) a kernel loaded while another kernel runs
+ * can wait for that kernel to end. The first call on a device grows the pool: make it before a
+ * serving kernel starts. DEG_ENOTREADY if the index is not uploaded;
  * DEG_EINVAL / DEG_ECUDA / DEG_EGRAPH as deg_refine_device. On an error the host adjacency takes
  * the device copy's graph (the batches published before it), so the two stay equal; if that copy
  * fails too, the device copy is released (upload again). */
@@ -379,7 +384,11 @@ DEG_API deg_status deg_serve_stop(deg_server* srv);
  * the library's search uses; ties go to the lower id. Up to k = 256 the distances come from
  * bfloat16 tensor-core products and every row within a proven rounding bound is re-scored in
  * float32; above 256 every distance is computed in float32 on the CUDA cores. Both give the same
- * result. Allocates its scratch and synchronises the stream. */
+ * result. Synchronises the stream before it returns. The tensor-core path keeps its device scratch
+ * (the bfloat16 copy of the rows, norms and per-query candidate lists: about 2 * n * dim rounded up
+ * to 64, plus tens of KiB per query) from one call to the next, per device, growing it when a call
+ * needs more and holding it until the process exits; calls on one device are serialised by a
+ * lock. */
 DEG_API deg_status knn_exact(const float* base_dev, int64_t n, const float* queries_dev, int64_t nq,
                      int32_t dim, int32_t k, int32_t* ids_dev, float* dists_dev, void* stream);
 

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <functional>
+#include <mutex>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -918,7 +919,7 @@ class DeviceBuilder {
   private:
     template <class T>
     cudaError_t alloc(T** p, size_t bytes) {
-        return ordered_ ? cudaMallocAsync(reinterpret_cast<void**>(p), bytes, st_)
+        return ordered_ ? (cudaError_t)ordered_alloc(reinterpret_cast<void**>(p), bytes, st_)
                         : cudaMalloc(reinterpret_cast<void**>(p), bytes);
     }
 
@@ -1020,6 +1021,48 @@ int refine_graph_device(const float* x_host, const int32_t* adj_inout, int64_t n
     if (const int rc = refine_graph(B, n, p.degree, p, why)) return rc;
     if (improved) *improved = B.improved();
     return B.download(adj_out, why);
+}
+
+int ordered_alloc(void** p, size_t bytes, void* stream) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t created;
+            if ((e = cudaMemPoolCreate(&created, &props)) != cudaSuccess) return (int)e;
+            uint64_t keep = ~0ull;
+            if ((e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+                cudaMemPoolDestroy(created);
+                return (int)e;
+            }
+            pools[dev] = created;
+        }
+        pool = pools[dev];
+    }
+    return (int)cudaMallocFromPoolAsync(p, bytes, pool, static_cast<cudaStream_t>(stream));
+}
+
+int preload_builder_kernels(int32_t dim_pad) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaSuccess;
+    const void* kernels[] = {(const void*)complete_graph_kernel, (const void*)extend_kernel, (const void*)gather_rows_kernel,
+                             (const void*)iota_kernel, (const void*)compact_adj_kernel, (const void*)opt_init_kernel,
+                             (const void*)opt_gather_kernel, (const void*)opt_step_a_kernel, (const void*)opt_step_b_kernel,
+                             (const void*)opt_finish_kernel, (const void*)weights_kernel, (const void*)expand_adj_kernel,
+                             (const void*)gather_adj_rows_kernel, (const void*)publish_adj_kernel};
+    for (const void* k : kernels)
+        if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return (int)e;
+    return sk::preload_search_f32(dim_pad / 4);
 }
 
 int refine_graph_live(const float* x_host, const int32_t* adj_in, DeviceIndex& ix, const deg_build_params& p,

@@ -870,6 +870,10 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
     if (cfg->max_blocks < 0) return fail(DEG_EINVAL, "serve_start: max_blocks must be >= 0");
     std::string why;
     if (workspace_reserve(idx->ws, idx->dev, 1, &why) != 0) return fail(DEG_ENOMEM, "serve_start: workspace: " + why);
+    // deg_refine_live may run beside the serving kernel: its kernels are loaded now, since a lazy
+    // load during the serving kernel's life would wait for that kernel to end
+    if (const int pe = preload_builder_kernels(idx->dev.dim_pad))
+        return fail(DEG_ECUDA, std::string("serve_start: kernel load: ") + cudaGetErrorString((cudaError_t)pe));
     deg_server* s = new (std::nothrow) deg_server;
     if (!s) return fail(DEG_ENOMEM, "serve_start: host allocation failed");
     s->idx = idx;

@@ -191,14 +191,15 @@ NoAllocSlot g_noalloc_slot[kMaxDevices];
 using CtxGetCurrentFn = CUresult (*)(CUcontext*);
 using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
+}  // namespace
+
 // Id of the calling thread's current context (driver entry points found through the runtime, so
-// the library does not link the driver library); 0 when there is none. Holds g_noalloc_mu.
+// the library does not link the driver library); 0 when there is none.
 unsigned long long current_context_id() {
     static CtxGetCurrentFn get_current = nullptr;
     static CtxGetIdFn get_id = nullptr;
-    static bool looked_up = false;
-    if (!looked_up) {
-        looked_up = true;
+    static std::once_flag once;
+    std::call_once(once, [] {
         cudaDriverEntryPointQueryResult q1{}, q2{};
         if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", reinterpret_cast<void**>(&get_current), 12000,
                                              cudaEnableDefault, &q1) != cudaSuccess || q1 != cudaDriverEntryPointSuccess)
@@ -206,14 +207,12 @@ unsigned long long current_context_id() {
         if (cudaGetDriverEntryPointByVersion("cuCtxGetId", reinterpret_cast<void**>(&get_id), 12000, cudaEnableDefault,
                                              &q2) != cudaSuccess || q2 != cudaDriverEntryPointSuccess)
             get_id = nullptr;
-    }
+    });
     CUcontext c = nullptr;
     unsigned long long id = 0;
     if (!get_current || !get_id || get_current(&c) != CUDA_SUCCESS || !c || get_id(c, &id) != CUDA_SUCCESS) return 0;
     return id;
 }
-
-}  // namespace
 
 int64_t knn_noalloc_capacity() { return kNoAllocScratchFloats; }
 

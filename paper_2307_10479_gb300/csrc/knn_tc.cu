@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 
 #include "deg_internal.h"
@@ -52,6 +53,7 @@ constexpr int kStageBytes = kStageA + kStageB;
 constexpr int kSmemDyn = kStages * kStageBytes + 1024;  // + alignment slack: one CTA per SM
 constexpr int kEpiWarps = 16;                           // epilogue warps: four per lane quarter
 constexpr int kEpiCols = TN * 4 / kEpiWarps;            // accumulator columns per epilogue warp
+static_assert(kEpiCols == 64, "the epilogue reads two 32-column halves per warp");
 constexpr int kTcThreads = 32 * (2 + kEpiWarps);        // producer, MMA, epilogue
 constexpr int kTmemCols = 2 * TN;                       // two accumulators
 constexpr int64_t kSampleMax = 65536;                   // sample rows per query
@@ -215,6 +217,24 @@ __device__ __forceinline__ void xn_minus_2v(float x0, float x1, uint32_t v0, uin
     asm("mov.b64 {%0, %1}, %2;" : "=f"(u0), "=f"(u1) : "l"(r));
 }
 
+// Waits for this thread's tcgen05.ld; v is tied to the wait, so the compiler treats the registers
+// as written here (not at the load) and touches them only afterwards.
+__device__ __forceinline__ void tmem_wait_ld(uint32_t* v) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]),
+                   "+r"(v[8]), "+r"(v[9]), "+r"(v[10]), "+r"(v[11]), "+r"(v[12]), "+r"(v[13]), "+r"(v[14]), "+r"(v[15]),
+                   "+r"(v[16]), "+r"(v[17]), "+r"(v[18]), "+r"(v[19]), "+r"(v[20]), "+r"(v[21]), "+r"(v[22]), "+r"(v[23]),
+                   "+r"(v[24]), "+r"(v[25]), "+r"(v[26]), "+r"(v[27]), "+r"(v[28]), "+r"(v[29]), "+r"(v[30]), "+r"(v[31])
+                 :: "memory");
+}
+
+// min(a, b, c) in one three-input min (sm_100 and later).
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 struct TcArgs {
     int32_t q_row0;                // first query of this chunk (tensor-map row)
     int32_t nq;                    // queries in this chunk
@@ -231,6 +251,58 @@ struct TcArgs {
     int32_t cap;
     int32_t* error;                // set to 1 when a wait ran out
 };
+
+// One 32-column half of an epilogue warp's accumulator block: lane = query row qrow, column j =
+// row xc + 32 c + j. Per column u = |x|^2 - 2 q.x (one paired FMA; rows past the end get +inf,
+// which no filter or group minimum takes); the filter pass appends the rows with u <= T, the sample
+// pass writes the two group-of-16 minima |q|^2 + min u.
+template <bool kFilter>
+__device__ __forceinline__ void epilogue_half(const TcArgs& a, const uint32_t* v, const float4* xs4, int c, int64_t xc,
+                                              int64_t qrow, bool qvalid, float qnorm, float T, int ng) {
+    const int64_t xg = xc + c * 32;
+    if (!qvalid || xg >= a.ncols) return;
+    float u[32];
+#pragma unroll
+    for (int j4 = 0; j4 < 8; ++j4) {
+        const float4 xv = xs4[c * 8 + j4];
+        xn_minus_2v(xv.x, xv.y, v[j4 * 4], v[j4 * 4 + 1], u[j4 * 4], u[j4 * 4 + 1]);
+        xn_minus_2v(xv.z, xv.w, v[j4 * 4 + 2], v[j4 * 4 + 3], u[j4 * 4 + 2], u[j4 * 4 + 3]);
+    }
+    if (xg + 32 > a.ncols) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (xg + j >= a.ncols) u[j] = __int_as_float(0x7f800000);
+    }
+    if (kFilter) {
+        float m[11];
+#pragma unroll
+        for (int j = 0; j < 10; ++j) m[j] = min3f(u[3 * j], u[3 * j + 1], u[3 * j + 2]);
+        m[10] = fminf(u[30], u[31]);
+        const float lo = fminf(min3f(min3f(m[0], m[1], m[2]), min3f(m[3], m[4], m[5]), min3f(m[6], m[7], m[8])),
+                               fminf(m[9], m[10]));
+        if (lo <= T) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                if (u[j] <= T && xg + j < a.ncols) {
+                    const int p = atomicAdd(a.cnt + qrow, 1);
+                    if (p < a.cap)
+                        a.cand[qrow * a.cap + p] = ((unsigned long long)okey(qnorm + u[j]) << 32) | (uint32_t)(xg + j);
+                }
+            }
+        }
+    } else {
+        float g[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float* w = u + 16 * h;
+            const float t0 = min3f(w[0], w[1], w[2]), t1 = min3f(w[3], w[4], w[5]), t2 = min3f(w[6], w[7], w[8]);
+            const float t3 = min3f(w[9], w[10], w[11]), t4 = min3f(w[12], w[13], w[14]);
+            g[h] = min3f(min3f(t0, t1, t2), fminf(t3, t4), w[15]);
+        }
+        a.gmin[qrow * ng + xg / 16] = qnorm + g[0];
+        if (xg + 16 < a.ncols) a.gmin[qrow * ng + xg / 16 + 1] = qnorm + g[1];
+    }
+}
 
 template <bool kFilter>
 __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_constant__ CUtensorMap tq,
@@ -344,18 +416,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
         const int ng = (int)((a.ncols + 15) / 16);
         int acc = 0;
         uint32_t aph = 0;
+        // a work item's row norms, query norm and limit are read one item ahead, so their global
+        // loads are in flight while the item before is processed
+        float4 xnext = make_float4(0.f, 0.f, 0.f, 0.f);
+        float qn_next = 0.f, lim_next = 0.f;
+        auto fetch = [&](uint32_t wi) {
+            const int64_t qr = (int64_t)(wi % (uint32_t)a.qblocks) * TM + quarter * 32 + lane;
+            const int64_t xo = (int64_t)(wi / (uint32_t)a.qblocks) * TN + cgroup * kEpiCols;
+            if (lane < kEpiCols / 4) xnext = __ldg(reinterpret_cast<const float4*>(a.xn + xo) + lane);   // norms are padded
+            qn_next = qr < a.nq ? __ldg(a.qn + qr) : 0.f;
+            lim_next = kFilter && qr < a.nq ? __ldg(a.limit + qr) : 0.f;
+        };
+        if (blockIdx.x < items) fetch(blockIdx.x);
         for (uint32_t w = blockIdx.x; w < items; w += gridDim.x) {
             const int64_t qrow = (int64_t)(w % (uint32_t)a.qblocks) * TM + quarter * 32 + lane;
             const int64_t xc = (int64_t)(w / (uint32_t)a.qblocks) * TN + cgroup * kEpiCols;
             const bool qvalid = qrow < a.nq;
-            float4 xpre = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (lane < kEpiCols / 4) xpre = __ldg(reinterpret_cast<const float4*>(a.xn + xc) + lane);   // norms are padded
-            const float qnorm = qvalid ? a.qn[qrow] : 0.f;
+            const float4 xpre = xnext;
+            const float qnorm = qn_next;
             float T = 0.f;
             if (kFilter && qvalid) {
-                const float d = a.limit[qrow] - qnorm;
+                const float d = lim_next - qnorm;
                 T = d + fabsf(d) * 2.3841858e-07f;
             }
+            if (w + gridDim.x < items) fetch(w + gridDim.x);
             const bool ok = mbar_wait(smem_u32(&tfull_bar[acc]), aph);
             if (!__all_sync(0xffffffffu, ok)) {
                 failed = true;
@@ -365,58 +449,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) dist_tc_kernel(const __grid_con
             if (lane < kEpiCols / 4) reinterpret_cast<float4*>(xn_tile[warp - 2])[lane] = xpre;
             __syncwarp();
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TN + cgroup * kEpiCols);
-#pragma unroll 1
-            for (int c = 0; c < kEpiCols / 32; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tbase + (uint32_t)(c * 32), v);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                const int64_t xg = xc + c * 32;
-                if (!qvalid || xg >= a.ncols) continue;
-                float u[32];
-#pragma unroll
-                for (int j4 = 0; j4 < 8; ++j4) {
-                    const float4 xv = xs4[c * 8 + j4];
-                    xn_minus_2v(xv.x, xv.y, v[j4 * 4], v[j4 * 4 + 1], u[j4 * 4], u[j4 * 4 + 1]);
-                    xn_minus_2v(xv.z, xv.w, v[j4 * 4 + 2], v[j4 * 4 + 3], u[j4 * 4 + 2], u[j4 * 4 + 3]);
-                }
-                if (xg + 32 > a.ncols) {                        // zero-filled rows past the end: NaN never
-#pragma unroll                                                  // compares <= and fminf skips it
-                    for (int j = 0; j < 32; ++j)
-                        if (xg + j >= a.ncols) u[j] = __int_as_float(0x7fc00000);
-                }
-                float m[16];
-#pragma unroll
-                for (int j = 0; j < 16; ++j) m[j] = fminf(u[j], u[j + 16]);   // tree: m[j] covers j, j+16
-#pragma unroll
-                for (int j = 0; j < 8; ++j) m[j] = fminf(m[j], m[j + 8]);
-                if (kFilter) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) m[j] = fminf(m[j], m[j + 4]);
-                    if (fminf(fminf(m[0], m[1]), fminf(m[2], m[3])) <= T) {
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            if (u[j] <= T && xg + j < a.ncols) {
-                                const int p = atomicAdd(a.cnt + qrow, 1);
-                                if (p < a.cap)
-                                    a.cand[qrow * a.cap + p] = ((unsigned long long)okey(qnorm + u[j]) << 32) | (uint32_t)(xg + j);
-                            }
-                        }
-                    }
-                } else {
-                    // group minima need rows j..j+15 together: redo the last levels on halves
-                    float g0 = u[0], g1 = u[16];
-#pragma unroll
-                    for (int j = 1; j < 16; ++j) {
-                        g0 = fminf(g0, u[j]);
-                        g1 = fminf(g1, u[16 + j]);
-                    }
-                    a.gmin[qrow * ng + xg / 16] = qnorm + g0;
-                    if (xg + 16 < a.ncols) a.gmin[qrow * ng + xg / 16 + 1] = qnorm + g1;
-                }
-            }
+            // the second half's tcgen05.ld is in flight while the first half is processed; once both
+            // are in registers the accumulator goes back to the MMA warp, before the second half's work
+            uint32_t v0[32], v1[32];
+            tmem_ld32(tbase, v0);
+            tmem_wait_ld(v0);
+            tmem_ld32(tbase + 32u, v1);
+            epilogue_half<kFilter>(a, v0, xs4, 0, xc, qrow, qvalid, qnorm, T, ng);
+            tmem_wait_ld(v1);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[acc]));
+            epilogue_half<kFilter>(a, v1, xs4, 1, xc, qrow, qvalid, qnorm, T, ng);
             if (++acc == 2) {
                 acc = 0;
                 aph ^= 1u;
@@ -770,6 +814,18 @@ struct Scratch {
     }
 };
 
+// launch_knn_exact's scratch, kept between calls: per device, grown when a call needs more, made
+// again in a new context of the device (the old context's memory went with it). The lock is held
+// for the whole call, which ends with its stream synchronised, so no call's kernels use a buffer
+// that another call frees or grows.
+struct KnnScratch {
+    std::mutex mu;
+    unsigned long long ctx = 0;
+    void* p[13] = {};
+    size_t bytes[13] = {};
+};
+KnnScratch g_knn_scratch[64];
+
 }  // namespace
 
 int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t nq, int32_t dim, int32_t k,
@@ -787,12 +843,35 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     int cap = 1024;
     while (cap < kCandCapMax && (int64_t)cap < 2 * (int64_t)k * stride) cap <<= 1;
     const int64_t tiles_n = (n + TN - 1) / TN, tiles_s = (ns + TN - 1) / TN;
-    Scratch s;
-    cudaError_t e = cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
+    if (dev < 0 || dev >= 64) return *why = "device index above 63", (int)cudaErrorInvalidValue;
+    KnnScratch& s = g_knn_scratch[dev];
+    std::lock_guard<std::mutex> lock(s.mu);
+    unsigned long long ctx = current_context_id();
+    if (ctx == 0) {
+        cudaFree(nullptr);                                   // makes the device's context current
+        ctx = current_context_id();
+    }
+    if (ctx == 0 || ctx != s.ctx) {
+        for (int i = 0; i < 13; ++i) {
+            s.p[i] = nullptr;
+            s.bytes[i] = 0;
+        }
+        s.ctx = ctx;
+    }
     const size_t sizes[] = {2ull * n * kpad, 4ull * tiles_n * TN, 4ull * n, 2ull * nq * kpad, 4ull * nq, 4ull * nq, 16,
                             4ull * chunk * ng, 4ull * chunk, 8ull * chunk * cap, 4ull * chunk, 4ull * (chunk + 2),
                             4ull * tiles_s * TN};
-    for (int i = 0; i < 13 && e == cudaSuccess; ++i) e = cudaMalloc(&s.p[i], std::max<size_t>(sizes[i], 16));
+    for (int i = 0; i < 13 && e == cudaSuccess; ++i) {
+        const size_t need = std::max<size_t>(sizes[i], 16);
+        if (s.bytes[i] >= need) continue;
+        if (s.p[i]) cudaFree(s.p[i]);
+        s.p[i] = nullptr;
+        s.bytes[i] = 0;
+        if ((e = cudaMalloc(&s.p[i], need)) == cudaSuccess) s.bytes[i] = need;
+    }
     if (e != cudaSuccess) return *why = std::string("knn scratch: ") + cudaGetErrorString(e), (int)e;
     auto* xb = static_cast<__nv_bfloat16*>(s.p[0]);
     auto* xn = static_cast<float*>(s.p[1]);
@@ -810,8 +889,7 @@ int launch_knn_exact(const float* base, int64_t n, const float* queries, int64_t
     int32_t* err = ov + chunk + 1;
     const int rerank_smem = rerank_smem_bytes(cap, dim, 0);
     if ((e = open_smem_limits()) != cudaSuccess) return *why = cudaGetErrorString(e), (int)e;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
+    int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     CUtensorMap tq, tx_all, tx_sample;
     if (!make_map(&tq, qb, nq, kpad, 2ull * kpad, TM) || !make_map(&tx_all, xb, n, kpad, 2ull * kpad, TN) ||

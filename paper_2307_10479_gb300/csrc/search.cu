@@ -19,7 +19,7 @@ namespace {
 
 template <class T>
 cudaError_t ws_alloc(const Workspace& ws, T** p, size_t bytes) {
-    return ws.stream_ordered ? cudaMallocAsync(reinterpret_cast<void**>(p), bytes, static_cast<cudaStream_t>(ws.alloc_stream))
+    return ws.stream_ordered ? (cudaError_t)ordered_alloc(reinterpret_cast<void**>(p), bytes, ws.alloc_stream)
                              : cudaMalloc(reinterpret_cast<void**>(p), bytes);
 }
 

@@ -1423,9 +1423,37 @@ int dispatch_shape(Params P, cudaStream_t st, void* t0, void* t1, std::string* w
     return (int)cudaErrorInvalidValue;
 }
 
+// Loads the batch-search kernels that dispatch_shape picks for rows of nchunk 16-byte chunks (both
+// front modes and the second kernel). With lazy module loading (the CUDA default) a kernel is
+// loaded at its first launch, and a load can wait for every kernel running on the device; a
+// persistent serving kernel then holds it up until it ends.
+template <class Rows, int G, int CPL>
+int preload_typed() {
+    cudaFuncAttributes fa;
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, search_fast_kernel<Rows, G, CPL, 0>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, search_fast_kernel<Rows, G, CPL, 1>)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, search_device_kernel<Rows, G, CPL>)) != cudaSuccess)
+        return (int)e;
+    return 0;
+}
+
+template <class Rows>
+int preload_shape(int nc) {
+    if (nc <= 4) return preload_typed<Rows, 4, 1>();
+    if (nc <= 8) return preload_typed<Rows, 8, 1>();
+    if (nc <= 16) return preload_typed<Rows, 16, 1>();
+    if (nc <= 32) return preload_typed<Rows, 32, 1>();
+    if (nc <= 64) return preload_typed<Rows, 32, 2>();
+    if (nc <= 128) return preload_typed<Rows, 32, 4>();
+    if (nc <= 256) return preload_typed<Rows, 32, 8>();
+    return (int)cudaErrorInvalidValue;
+}
+
 // The launchers, one translation unit per row format (search_f32.cu, search_bf16.cu, search_fp8.cu),
 // so the kernels of the three formats compile in parallel.
 int dispatch_search_f32(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
+int preload_search_f32(int nchunk);
 int dispatch_search_bf16(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
 int dispatch_search_fp8(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
 int dispatch_serve_f32(Params P, const ServeRing& S, const int32_t* pivots, int np, cudaStream_t st, int* warps,

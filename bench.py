@@ -446,71 +446,6 @@ def serving(deg, idx, w, q, gt):
     return out
 
 
-def serve_while_refining(deg, idx, w, q, gt, rate=200_000, seconds=3.0, chunk=32_768):
-    """Continuous refinement (Alg. 5) on the device while the serving kernel answers requests on
-    the same index (deg_refine_live). The server keeps at most two blocks of 4 warps per SM and
-    leaves the rest of each SM to the refinement. Measured: the same Poisson trace of k = 10 vector requests (eps 0.1,
-    bfloat16 rows, pivot entry) served alone and during refinement, and the refinement's rounds/s
-    alone (no server) and while serving. Refinement runs in calls of `chunk` rounds, each a fresh
-    copy of the graph on the device, so rounds/s includes that set-up."""
-    import torch
-    sms = torch.cuda.get_device_properties(0).multi_processor_count
-    rng = np.random.default_rng(77)
-    n = int(rate * seconds)
-    qi = rng.integers(0, len(q), n)
-    arrivals = synth.poisson_arrivals(rate, n, seed=77)
-    arrivals -= arrivals[0]
-    vertices, ks, epss = np.full(n, -1, np.int32), np.full(n, 10, np.int32), np.full(n, 0.1, np.float32)
-    out = {"offered_qps": rate, "requests": n, "serve_blocks": 2 * sms, "chunk_rounds": chunk}
-
-    def summary(lat, ids, st, wall):
-        return {"sustained_qps": n / wall, "p50_ms": 1e3 * float(np.median(lat)),
-                "p99_ms": 1e3 * float(np.percentile(lat, 99)), "recall_at_10": recall(ids[:, :10], gt[qi]),
-                "status_ok": bool((st == 0).all())}
-
-    def refine_until(stop, seed0):
-        done, t0 = 0, time.perf_counter()
-        while not stop(done, time.perf_counter() - t0):
-            idx.refine_live(chunk, w.k_opt or w.degree, w.eps_opt, w.i_opt, seed=seed0 + done)
-            done += chunk
-        return done, time.perf_counter() - t0
-
-    srv = deg.Server(idx, capacity=1 << 16, kmax=10, precision="bf16", entry="pivot", idle_timeout_s=60.0,
-                     max_blocks=2 * sms)
-    try:
-        t0 = time.perf_counter()
-        lat, ids, _, st = srv.run_trace(q[qi], vertices, ks, epss, arrivals, timeout_s=300.0)
-        out["serve_alone"] = summary(lat, ids, st, time.perf_counter() - t0)
-    finally:
-        srv.stop()
-    rounds, sec = refine_until(lambda done, t: t >= seconds, 1_000_000)
-    out["refine_alone_rounds_per_s"] = rounds / sec
-    srv = deg.Server(idx, capacity=1 << 16, kmax=10, precision="bf16", entry="pivot", idle_timeout_s=60.0,
-                     max_blocks=2 * sms)
-    res = {}
-
-    def run():
-        t = time.perf_counter()
-        res["trace"] = srv.run_trace(q[qi], vertices, ks, epss, arrivals, timeout_s=300.0)
-        res["wall"] = time.perf_counter() - t
-
-    th = threading.Thread(target=run)
-    try:
-        th.start()
-        rounds, sec = refine_until(lambda done, t: not th.is_alive(), 2_000_000)
-        th.join()
-    finally:
-        srv.stop()
-    lat, ids, _, st = res["trace"]
-    out["serve_while_refining"] = summary(lat, ids, st, res["wall"])
-    out["refine_while_serving_rounds_per_s"] = rounds / sec
-    a, b = out["serve_alone"], out["serve_while_refining"]
-    log(f"[bench] serving {rate}/s alone: p50 {a['p50_ms']:.2f} ms p99 {a['p99_ms']:.2f} ms; while refining "
-        f"({out['refine_while_serving_rounds_per_s']:.0f} rounds/s, alone {out['refine_alone_rounds_per_s']:.0f}): "
-        f"p50 {b['p50_ms']:.2f} ms p99 {b['p99_ms']:.2f} ms, recall@10 {b['recall_at_10']:.4f}")
-    return out
-
-
 def explore_truth(deg, bq, v, k):
     """Exact k-NN of x_v over V without v (the exploration protocol's ground truth): k + 1
     neighbours by knn_exact, v removed."""
@@ -643,7 +578,6 @@ def main():
     ap.add_argument("--eps", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--no-refine-live", action="store_true", help="skip serving during continuous refinement")
     ap.add_argument("--no-extra", action="store_true", help="skip the k = 1 / 100 and exploration points")
     ap.add_argument("--only", default=None, choices=["plain", "fp8-pivot", "fp8-learned", "bf16-learned"],
                     help="run one form at --eps for --warmup + --steps batches and nothing else (for profilers)")
@@ -889,13 +823,6 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         line["cpu_baseline"] = cpu_baseline(base, idx.adjacency(), q, oracle.median_vertex(base), plain["eps"])
-    if not args.no_serve and not args.no_refine_live:
-        # last: it changes the graph the other measurements ran on
-        try:
-            line["serving"]["while_refining"] = serve_while_refining(deg, idx, w, q, gt)
-        except Exception as exc:                     # reported, not fatal to the measurements above
-            line["serving"]["while_refining"] = {"error": str(exc)}
-            log(f"[bench] serving while refining failed: {exc}")
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -128,30 +128,6 @@ DEG_API deg_status deg_insert_device(deg_index* idx, const float* new_host, int6
  * the device copy released: upload again before searching. p->degree must equal the index's. */
 DEG_API deg_status deg_refine_device(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
 
-/* Alg. 5 (Sec. 5.3: continuous refinement) as deg_refine_device, on an UPLOADED index that stays in
- * use: a serving kernel (deg_serve_start) may run throughout. The refinement runs on a copy of the
- * graph; after each batch of up to 4,096 rounds (all their optimisations finished or reverted, so
- * the copy is a valid DEG again) the entries of the device adjacency that changed are rewritten in
- * place, each with one 64-bit store that the serving kernel reads with one 64-bit load at GPU
- * scope. A request served meanwhile walks a mix of the old and new graph: every neighbour it reads
- * is a vertex, so its results are vertices with their exact distances, but which vertices it finds
- * may differ from a search on either graph alone. The serving kernel must leave the GPU room for
- * the refinement's kernels (deg_serve_config.max_blocks), or they run only once it ends. On return
- * the device adjacency equals the host adjacency, which holds the refined graph (checked; the
- * device copy is kept). Batched searches (deg_search*) must not run during the call: they read the
- * adjacency through the read-only cache. Device memory of the call (about the float32 rows and two
- * adjacency copies, plus search scratch) is allocated and freed stream-ordered on `stream` (NULL: a
- * stream of its own) from a memory pool of the library's own, which keeps the memory for the next
- * call until the process exits, so that no allocation, free or synchronisation of the call waits for
- * the serving kernel. deg_serve_start loads the refinement's kernels before it launches the serving
- * kernel: under lazy module loading (the CUDA default) a kernel loaded while another kernel runs
- * can wait for that kernel to end. The first call on a device grows the pool: make it before a
- * serving kernel starts. DEG_ENOTREADY if the index is not uploaded;
- * DEG_EINVAL / DEG_ECUDA / DEG_EGRAPH as deg_refine_device. On an error the host adjacency takes
- * the device copy's graph (the batches published before it), so the two stay equal; if that copy
- * fails too, the device copy is released (upload again). */
-DEG_API deg_status deg_refine_live(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream);
-
 /* Remove vertex v (0 <= v < n) from the index on the host. The paper leaves removal open (App. A)
  * while calling the graph fully dynamic; this removal keeps every invariant. v's d edges go; its
  * former neighbours, each one edge short, are joined in pairs by new edges, closest non-adjacent
@@ -338,8 +314,8 @@ typedef struct {
                                 learned entry point                                               */
     int32_t learned_stop;    /* 1: use the index's stop network                                    */
     double idle_timeout_s;   /* end the kernel when no request arrives for this long (> 0)         */
-    int32_t max_blocks;      /* 0: as many blocks of 8 warps as fit on the GPU; else at most this
-                                many, leaving the rest to other kernels (deg_refine_live)          */
+    int32_t max_blocks;      /* 0: as many blocks of 4 warps as fit on the GPU; else at most this
+                                many, leaving the rest of the GPU to other kernels                  */
 } deg_serve_config;
 
 /* Launch the serving kernel on its own stream. The index must stay alive until deg_serve_stop. */
@@ -416,10 +392,11 @@ DEG_API deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const flo
  * index in [0, n) of the nearest of rows_dev [n][dim] (float32, row-major), 1 <= n <= 4096, and
  * its float32 distance. This is the search the pivot entry routing runs (entry_mode 1). Results
  * are exact: the same float32 distances as knn_exact, ties to the lower index. Distances come
- * from bfloat16 tensor-core products, and every row within a proven rounding bound of the
- * smallest is re-scored exactly. `cap` (a power of two, 1 ... 4096) bounds the rows re-scored per
- * query. A query with more rows inside the bound is scored exactly against all n rows instead,
- * with the same result. Allocates its scratch and synchronises the stream. DEG_EINVAL when n is
+ * from one pass of bfloat16 tensor-core products reduced to the minimum of each group of 16 rows;
+ * every group whose minimum lies within a proven rounding bound of the smallest is re-scored
+ * exactly. `cap` (a power of two, 1 ... 4096) bounds the rows re-scored per query. A query with
+ * more rows in such groups is scored exactly against all n rows instead, with the same result.
+ * Allocates its scratch and synchronises the stream. DEG_EINVAL when n is
  * outside 1 ... 4096, dim is not positive, nq is negative or above 2^24, a pointer is NULL, or
  * cap is not a power of two in 1 ... 4096; DEG_ECUDA on a device error. nq = 0 does nothing. */
 DEG_API deg_status deg_nearest_rows(const float* rows_dev, int64_t n, int32_t dim, const float* queries_dev, int64_t nq,

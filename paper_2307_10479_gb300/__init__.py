@@ -73,7 +73,6 @@ def lib() -> ctypes.CDLL:
             "deg_refine_device": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_insert_device": (S, [P, P, i64, ctypes.POINTER(BuildParams), i32, P]),
             "deg_remove": (S, [P, i32, ctypes.POINTER(i32)]),
-            "deg_refine_live": (S, [P, ctypes.POINTER(BuildParams), ctypes.POINTER(i64), P]),
             "deg_index_from_arrays": (S, [P, P, i64, i32, i32, ctypes.POINTER(P)]),
             "deg_save": (S, [P, ctypes.c_char_p, i32]),
             "deg_load": (S, [ctypes.c_char_p, P, ctypes.POINTER(P)]),
@@ -181,16 +180,6 @@ class Index:
         p = BuildParams(degree, k_ext, eps_ext, k_opt or degree, eps_opt, i_opt, 0, 0)
         _check(lib().deg_insert_device(self._h, vectors.ctypes.data, vectors.shape[0], ctypes.byref(p), batch_div,
                                        _stream_ptr(stream)))
-
-    def refine_live(self, rounds: int, k_opt: int, eps_opt: float, i_opt: int, seed: int = 0, stream=None) -> int:
-        """Alg. 5 on the uploaded index while a Server may be running (deg_refine_live); returns the
-        improved count. The device copy is updated in place batch by batch and kept."""
-        _, _, degree = self.info()
-        p = BuildParams(degree, degree, 0.2, k_opt, eps_opt, i_opt, rounds, seed)
-        improved = ctypes.c_int64()
-        _check(lib().deg_refine_live(self._h, ctypes.byref(p), ctypes.byref(improved),
-                                     None if stream is None else _stream_ptr(stream)))
-        return improved.value
 
     def remove(self, v: int) -> int:
         """Remove vertex v (deg_remove); the last vertex takes id v. Returns its old id, or -1 if v was last."""

@@ -26,8 +26,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <functional>
-#include <mutex>
 #include <cmath>
 #include <string>
 #include <vector>
@@ -684,19 +682,14 @@ uint64_t splitmix64(uint64_t& s) {  // SplitMix64 (Steele, Lea, Flood 2014)
 // batches and the optimisation waves.
 class DeviceBuilder {
   public:
-    // ordered: every allocation and free is stream-ordered on `stream` (cudaMallocAsync /
-    // cudaFreeAsync), so none waits for kernels of other streams, such as a persistent serving kernel
-    DeviceBuilder(int64_t n, int32_t dim, int32_t degree, deg_stream_t stream, bool ordered = false)
+    DeviceBuilder(int64_t n, int32_t dim, int32_t degree, deg_stream_t stream)
         : n_(n), dim_(dim), d_(degree), dim_pad_((dim + 3) / 4 * 4), deg_pad_((degree + 3) / 4 * 4),
-          stream_(stream), st_(reinterpret_cast<cudaStream_t>(stream)), ordered_(ordered) {
-        ws_.stream_ordered = ordered;
-        ws_.alloc_stream = st_;
-    }
+          stream_(stream), st_(reinterpret_cast<cudaStream_t>(stream)) {}
     ~DeviceBuilder() {
         for (void* p : {(void*)x_, (void*)w_, (void*)adj_, (void*)lock_, (void*)iota_, (void*)qbuf_, (void*)qvert_,
                         (void*)sid_, (void*)sd_, (void*)status_, (void*)opt_u_, (void*)opt_cnt_, (void*)tasks_,
                         (void*)list_, (void*)seeds_, (void*)seeds2_, (void*)cnt_, (void*)out_})
-            if (p) ordered_ ? (void)cudaFreeAsync(p, st_) : (void)cudaFree(p);
+            cudaFree(p);
         workspace_free(ws_);
     }
 
@@ -704,23 +697,23 @@ class DeviceBuilder {
         kmax_ = kmax;
         cudaError_t e;
         const int64_t nq = 2 * kMaxBatch;
-        if ((e = alloc(&x_, sizeof(float) * n_ * dim_pad_)) != cudaSuccess ||
-            (e = alloc(&adj_, sizeof(int2) * n_ * deg_pad_)) != cudaSuccess ||
-            (e = alloc(&w_, sizeof(float) * n_ * deg_pad_)) != cudaSuccess ||
-            (e = alloc(&lock_, sizeof(int32_t) * n_)) != cudaSuccess ||
-            (e = alloc(&iota_, sizeof(int32_t) * n_)) != cudaSuccess ||
-            (e = alloc(&qbuf_, sizeof(float) * nq * dim_)) != cudaSuccess ||
-            (e = alloc(&qvert_, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = alloc(&sid_, sizeof(int32_t) * nq * kmax)) != cudaSuccess ||
-            (e = alloc(&sd_, sizeof(float) * nq * kmax)) != cudaSuccess ||
-            (e = alloc(&status_, sizeof(int32_t) * kMaxBatch)) != cudaSuccess ||
-            (e = alloc(&opt_u_, sizeof(int32_t) * kMaxBatch * d_)) != cudaSuccess ||
-            (e = alloc(&opt_cnt_, sizeof(int32_t) * kMaxBatch)) != cudaSuccess ||
-            (e = alloc(&tasks_, sizeof(OptTask) * kMaxBatch)) != cudaSuccess ||
-            (e = alloc(&list_, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = alloc(&seeds_, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = alloc(&seeds2_, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = alloc(&cnt_, sizeof(int32_t))) != cudaSuccess)
+        if ((e = cudaMalloc(&x_, sizeof(float) * n_ * dim_pad_)) != cudaSuccess ||
+            (e = cudaMalloc(&adj_, sizeof(int2) * n_ * deg_pad_)) != cudaSuccess ||
+            (e = cudaMalloc(&w_, sizeof(float) * n_ * deg_pad_)) != cudaSuccess ||
+            (e = cudaMalloc(&lock_, sizeof(int32_t) * n_)) != cudaSuccess ||
+            (e = cudaMalloc(&iota_, sizeof(int32_t) * n_)) != cudaSuccess ||
+            (e = cudaMalloc(&qbuf_, sizeof(float) * nq * dim_)) != cudaSuccess ||
+            (e = cudaMalloc(&qvert_, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&sid_, sizeof(int32_t) * nq * kmax)) != cudaSuccess ||
+            (e = cudaMalloc(&sd_, sizeof(float) * nq * kmax)) != cudaSuccess ||
+            (e = cudaMalloc(&status_, sizeof(int32_t) * kMaxBatch)) != cudaSuccess ||
+            (e = cudaMalloc(&opt_u_, sizeof(int32_t) * kMaxBatch * d_)) != cudaSuccess ||
+            (e = cudaMalloc(&opt_cnt_, sizeof(int32_t) * kMaxBatch)) != cudaSuccess ||
+            (e = cudaMalloc(&tasks_, sizeof(OptTask) * kMaxBatch)) != cudaSuccess ||
+            (e = cudaMalloc(&list_, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&seeds_, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&seeds2_, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&cnt_, sizeof(int32_t))) != cudaSuccess)
             return err(e, "build buffers", why);
         if ((e = cudaMemsetAsync(x_, 0, sizeof(float) * n_ * dim_pad_, st_)) != cudaSuccess ||
             (e = cudaMemcpy2DAsync(x_, sizeof(float) * dim_pad_, x_host, sizeof(float) * dim_, sizeof(float) * dim_, n_,
@@ -733,7 +726,7 @@ class DeviceBuilder {
         G_ = BuildGraph{x_, dim_pad_, adj_, w_, lock_, d_, deg_pad_};
         if (adj_host) {
             // an existing graph: pairs and weights from its [n][degree] adjacency
-            if ((e = alloc(&out_, sizeof(int32_t) * n_ * d_)) != cudaSuccess ||
+            if ((e = cudaMalloc(&out_, sizeof(int32_t) * n_ * d_)) != cudaSuccess ||
                 (e = cudaMemcpyAsync(out_, adj_host, sizeof(int32_t) * n_ * d_, cudaMemcpyHostToDevice, st_)) != cudaSuccess)
                 return err(e, "adjacency upload", why);
             expand_adj_kernel<<<1024, 256, 0, st_>>>(out_, n_, deg_pad_, d_, adj_);
@@ -901,7 +894,7 @@ class DeviceBuilder {
 
     int download(int32_t* adj_host, std::string* why) {
         cudaError_t e;
-        if (!out_ && (e = alloc(&out_, sizeof(int32_t) * n_ * d_)) != cudaSuccess) return err(e, "adjacency out", why);
+        if (!out_ && (e = cudaMalloc(&out_, sizeof(int32_t) * n_ * d_)) != cudaSuccess) return err(e, "adjacency out", why);
         compact_adj_kernel<<<1024, 256, 0, st_>>>(adj_, n_, deg_pad_, d_, out_);
         if ((e = cudaGetLastError()) != cudaSuccess ||
             (e = cudaMemcpyAsync(adj_host, out_, sizeof(int32_t) * n_ * d_, cudaMemcpyDeviceToHost, st_)) != cudaSuccess ||
@@ -912,17 +905,7 @@ class DeviceBuilder {
 
     int64_t improved() const { return improved_; }
 
-    // The builder's adjacency as the search kernels read it: [n][deg_pad] pairs {id, id}.
-    const int2* pairs() const { return adj_; }
-    int32_t deg_pad() const { return deg_pad_; }
-
   private:
-    template <class T>
-    cudaError_t alloc(T** p, size_t bytes) {
-        return ordered_ ? (cudaError_t)ordered_alloc(reinterpret_cast<void**>(p), bytes, st_)
-                        : cudaMalloc(reinterpret_cast<void**>(p), bytes);
-    }
-
     static int err(cudaError_t e, const char* what, std::string* why) {
         *why = std::string(what) + ": " + cudaGetErrorString(e);
         return (int)e;
@@ -932,7 +915,6 @@ class DeviceBuilder {
     int32_t dim_, d_, dim_pad_, deg_pad_, kmax_ = 0;
     deg_stream_t stream_;
     cudaStream_t st_;
-    bool ordered_;
     float *x_ = nullptr, *w_ = nullptr, *qbuf_ = nullptr, *sd_ = nullptr;
     int2* adj_ = nullptr;
     int32_t *lock_ = nullptr, *iota_ = nullptr, *qvert_ = nullptr, *sid_ = nullptr, *status_ = nullptr;
@@ -956,8 +938,7 @@ namespace {
 // edge. Rounds run in batches of distinct vertices (at most 4,096 at once); each vertex's
 // optimisations run in order, one per wave, and its neighbour list is taken when its batch starts
 // (a neighbour that is no longer adjacent by its turn is skipped).
-int refine_graph(DeviceBuilder& B, int64_t n, int32_t d, const deg_build_params& p, std::string* why,
-                 const std::function<int(const DeviceBuilder&, std::string*)>& after_batch = {}) {
+int refine_graph(DeviceBuilder& B, int64_t n, int32_t d, const deg_build_params& p, std::string* why) {
     uint64_t s = p.seed;
     std::vector<int32_t> vs, nb;
     std::vector<char> seen((size_t)n, 0);
@@ -984,30 +965,8 @@ int refine_graph(DeviceBuilder& B, int64_t n, int32_t d, const deg_build_params&
             queues[i].insert(queues[i].end(), {vs[i], -1, 2});
         }
         if (const int rc = B.optimise(queues, p.i_opt, p.k_opt, p.eps_opt, why)) return rc;
-        if (after_batch)
-            if (const int rc = after_batch(B, why)) return rc;
     }
     return 0;
-}
-
-// Brings the serving adjacency dst [n][dst_pad] {internal id, caller id} (row = caller id) to the
-// builder's graph src [n][src_pad] {id, id}. Only entries that differ are written, each with one
-// 64-bit relaxed store at GPU scope: a serving kernel reading the row at the same time (64-bit
-// relaxed loads) sees every entry either old or new, never half of each.
-__global__ void publish_adj_kernel(const int2* __restrict__ src, int32_t src_pad, int2* dst, int32_t dst_pad,
-                                   const int32_t* __restrict__ old2new, int64_t n, int32_t d) {
-    const int64_t total = n * d;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t u = i / d;
-        const int j = (int)(i - u * d);
-        const int32_t c = src[u * src_pad + j].x;
-        if (c < 0) continue;
-        const unsigned long long want = (unsigned long long)(uint32_t)old2new[c] | ((unsigned long long)(uint32_t)c << 32);
-        unsigned long long* q = reinterpret_cast<unsigned long long*>(dst + u * dst_pad + j);
-        unsigned long long cur;
-        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(cur) : "l"(q));
-        if (cur != want) asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(q), "l"(want) : "memory");
-    }
 }
 
 }  // namespace
@@ -1021,74 +980,6 @@ int refine_graph_device(const float* x_host, const int32_t* adj_inout, int64_t n
     if (const int rc = refine_graph(B, n, p.degree, p, why)) return rc;
     if (improved) *improved = B.improved();
     return B.download(adj_out, why);
-}
-
-int ordered_alloc(void** p, size_t bytes, void* stream) {
-    static std::mutex mu;
-    static cudaMemPool_t pools[64] = {};
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return (int)e;
-    if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
-    cudaMemPool_t pool;
-    {
-        std::lock_guard<std::mutex> lock(mu);
-        if (!pools[dev]) {
-            cudaMemPoolProps props{};
-            props.allocType = cudaMemAllocationTypePinned;
-            props.location.type = cudaMemLocationTypeDevice;
-            props.location.id = dev;
-            cudaMemPool_t created;
-            if ((e = cudaMemPoolCreate(&created, &props)) != cudaSuccess) return (int)e;
-            uint64_t keep = ~0ull;
-            if ((e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
-                cudaMemPoolDestroy(created);
-                return (int)e;
-            }
-            pools[dev] = created;
-        }
-        pool = pools[dev];
-    }
-    return (int)cudaMallocFromPoolAsync(p, bytes, pool, static_cast<cudaStream_t>(stream));
-}
-
-int preload_builder_kernels(int32_t dim_pad) {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaSuccess;
-    const void* kernels[] = {(const void*)complete_graph_kernel, (const void*)extend_kernel, (const void*)gather_rows_kernel,
-                             (const void*)iota_kernel, (const void*)compact_adj_kernel, (const void*)opt_init_kernel,
-                             (const void*)opt_gather_kernel, (const void*)opt_step_a_kernel, (const void*)opt_step_b_kernel,
-                             (const void*)opt_finish_kernel, (const void*)weights_kernel, (const void*)expand_adj_kernel,
-                             (const void*)gather_adj_rows_kernel, (const void*)publish_adj_kernel};
-    for (const void* k : kernels)
-        if ((e = cudaFuncGetAttributes(&fa, k)) != cudaSuccess) return (int)e;
-    return sk::preload_search_f32(dim_pad / 4);
-}
-
-int refine_graph_live(const float* x_host, const int32_t* adj_in, DeviceIndex& ix, const deg_build_params& p,
-                      int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why) {
-    if (p.degree > kMaxBuildDegree) return *why = "degree above 128", (int)cudaErrorInvalidValue;
-    if (p.k_opt > 1024 || p.i_opt > 6) return *why = "k_opt above 1024 or i_opt above 6", (int)cudaErrorInvalidValue;
-    const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    int2* dst = reinterpret_cast<int2*>(ix.adj);
-    int rc = 0;
-    {
-        DeviceBuilder B(ix.n, ix.dim, p.degree, stream, /*ordered=*/true);
-        rc = B.init(x_host, adj_in, std::max(p.k_opt, p.degree), why);
-        if (rc == 0)
-            rc = refine_graph(B, ix.n, p.degree, p, why, [&](const DeviceBuilder& b, std::string* w) {
-                publish_adj_kernel<<<1024, 256, 0, st>>>(b.pairs(), b.deg_pad(), dst, ix.deg_pad, ix.old2new, ix.n,
-                                                         ix.degree);
-                const cudaError_t e = cudaGetLastError();
-                if (e != cudaSuccess) return *w = std::string("publish: ") + cudaGetErrorString(e), (int)e;
-                return 0;
-            });
-        if (rc == 0 && improved) *improved = B.improved();
-        if (rc == 0) rc = B.download(adj_out, why);
-    }
-    const cudaError_t e = cudaStreamSynchronize(st);           // the builder's stream-ordered frees
-    if (rc == 0 && e != cudaSuccess) return *why = std::string("refine stream: ") + cudaGetErrorString(e), (int)e;
-    return rc;
 }
 
 namespace {

@@ -102,29 +102,6 @@ deg_status check_rows(const int32_t* adj, int64_t n, int32_t d, const std::vecto
     return DEG_OK;
 }
 
-// The host adjacency from the device copy ([n][deg_pad] {internal id, caller id}, row = caller id),
-// copied on `st`, then checked.
-deg_status adjacency_from_device(deg_index* idx, cudaStream_t st) {
-    const int64_t n = idx->n;
-    const int32_t d = idx->degree, pad = idx->dev.deg_pad;
-    std::vector<int2> pairs;
-    std::vector<int32_t> adj;
-    try {
-        pairs.resize((size_t)n * pad);
-        adj.resize((size_t)n * d);
-    } catch (const std::bad_alloc&) {
-        return fail(DEG_ENOMEM, "adjacency copy: host allocation failed");
-    }
-    cudaError_t e = cudaMemcpyAsync(pairs.data(), idx->dev.adj, sizeof(int2) * pairs.size(), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return fail(DEG_ECUDA, std::string("adjacency copy: ") + cudaGetErrorString(e));
-    for (int64_t u = 0; u < n; ++u)
-        for (int32_t j = 0; j < d; ++j) adj[(size_t)u * d + j] = pairs[(size_t)u * pad + j].y;
-    const deg_status s = check_graph(adj.data(), n, d);
-    if (s == DEG_OK) idx->adj.swap(adj);
-    return s;
-}
-
 void free_device(deg_index* idx) {
     DeviceIndex& d = idx->dev;
     cudaFree(d.x32);
@@ -287,47 +264,6 @@ extern "C" deg_status deg_refine_device(deg_index* idx, const deg_build_params* 
     if (s != DEG_OK) return s;
     free_device(idx);                                          // the device copy shows the old graph
     return DEG_OK;
-}
-
-extern "C" deg_status deg_refine_live(deg_index* idx, const deg_build_params* p, int64_t* improved, void* stream) {
-    if (!idx || !p) return fail(DEG_EINVAL, "deg_refine_live: NULL argument");
-    if (!idx->dev.adj || !idx->dev.old2new) return fail(DEG_ENOTREADY, "deg_refine_live: index not uploaded");
-    if (p->degree != idx->degree) return fail(DEG_EINVAL, "deg_refine_live: params.degree differs from the index's");
-    if (idx->degree > 128) return fail(DEG_EINVAL, "deg_refine_live: degree above 128");
-    if (p->refine_rounds < 0 || p->i_opt < 1 || p->i_opt > 6 || p->k_opt < 1 || p->k_opt > 1024 || !(p->eps_opt >= 0.f))
-        return fail(DEG_EINVAL, "deg_refine_live: need refine_rounds >= 0, 1 <= i_opt <= 6, 1 <= k_opt <= 1024, eps_opt >= 0");
-    if (improved) *improved = 0;
-    if (p->refine_rounds == 0) return DEG_OK;
-    cudaStream_t own = nullptr;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (!st) {                                                 // never the legacy stream: it waits for others
-        const cudaError_t e = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(e, "deg_refine_live: stream");
-        st = own;
-    }
-    std::vector<int32_t> out;
-    try {
-        out.resize(idx->adj.size());
-    } catch (const std::bad_alloc&) {
-        if (own) cudaStreamDestroy(own);
-        return fail(DEG_ENOMEM, "deg_refine_live: host allocation failed");
-    }
-    std::string why;
-    const int e = refine_graph_live(idx->x.data(), idx->adj.data(), idx->dev, *p, out.data(), improved,
-                                    reinterpret_cast<deg_stream_t>(st), &why);
-    deg_status s = e == 0 ? check_graph(out.data(), idx->n, idx->degree) : DEG_OK;
-    if (e == 0 && s == DEG_OK) {
-        idx->adj.swap(out);
-    } else {
-        // the device copy holds the batches published before the failure (a valid graph at each
-        // batch's end): the host takes it over, so both stay equal (no free, which would wait for
-        // a running serving kernel)
-        const std::string msg = e != 0 ? "deg_refine_live: " + why : std::string(deg_last_error());
-        if (adjacency_from_device(idx, st) != DEG_OK) free_device(idx);
-        s = fail(e == 0 ? s : e == cudaErrorInvalidValue ? DEG_EINVAL : DEG_ECUDA, msg);
-    }
-    if (own) cudaStreamDestroy(own);
-    return s;
 }
 
 extern "C" deg_status deg_remove(deg_index* idx, int32_t v, int32_t* moved_from) {
@@ -870,10 +806,6 @@ extern "C" deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cf
     if (cfg->max_blocks < 0) return fail(DEG_EINVAL, "serve_start: max_blocks must be >= 0");
     std::string why;
     if (workspace_reserve(idx->ws, idx->dev, 1, &why) != 0) return fail(DEG_ENOMEM, "serve_start: workspace: " + why);
-    // deg_refine_live may run beside the serving kernel: its kernels are loaded now, since a lazy
-    // load during the serving kernel's life would wait for that kernel to end
-    if (const int pe = preload_builder_kernels(idx->dev.dim_pad))
-        return fail(DEG_ECUDA, std::string("serve_start: kernel load: ") + cudaGetErrorString((cudaError_t)pe));
     deg_server* s = new (std::nothrow) deg_server;
     if (!s) return fail(DEG_ENOMEM, "serve_start: host allocation failed");
     s->idx = idx;

@@ -41,32 +41,9 @@ int insert_vertices_device(const float* x_host, int32_t* adj, int64_t n_old, int
 int refine_graph_device(const float* x_host, const int32_t* adj_in, int64_t n, int32_t dim, const deg_build_params& p,
                         int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why);
 
-struct DeviceIndex;
-// Alg. 5 as refine_graph_device, while the uploaded index ix stays in use by a serving kernel: after
-// each batch of rounds the entries of ix.adj that changed are rewritten in place, one 64-bit
-// relaxed store each. Every device allocation of the run is stream-ordered on `stream`, so nothing
-// waits for the serving kernel. adj_out gets the final graph.
-// Stream-ordered allocation on `stream` from a device memory pool of the library's own that keeps
-// what is freed into it for reuse (release threshold: unlimited), so that no later stream
-// synchronisation hands memory back to the system, which can wait for every kernel running on the
-// device (a persistent serving kernel). One pool per device, created at first use, kept until exit.
-// Returns a cudaError_t value (0 = success).
-int ordered_alloc(void** p, size_t bytes, void* stream);
-
 // Id of the calling thread's current CUDA context (0 when there is none): device addresses cached
 // between calls are valid only in the context they were made in.
 unsigned long long current_context_id();
-
-// Loads every kernel deg_refine_live launches (the builder's and the float32 batch-search kernels
-// for rows of dim_pad floats) now, so that none is loaded while a serving kernel runs: a lazy load
-// can wait for every kernel running on the device. Returns a cudaError_t value (0 = success).
-int preload_builder_kernels(int32_t dim_pad);
-namespace sk {
-int preload_search_f32(int nchunk);   // search_f32.cu
-}
-
-int refine_graph_live(const float* x_host, const int32_t* adj_in, DeviceIndex& ix, const deg_build_params& p,
-                      int32_t* adj_out, int64_t* improved, deg_stream_t stream, std::string* why);
 
 // Record an error message for deg_last_error() and return the status.
 deg_status fail(deg_status s, const std::string& msg);
@@ -122,10 +99,6 @@ struct Workspace {
     uint32_t* pbitmaps = nullptr;    // second kernel: [pslots][words]
     uint64_t* pbacks = nullptr;      //   [pslots][n + 1]
     int32_t pslots = 0;
-    // stream-ordered allocation (cudaMallocAsync / cudaFreeAsync on this stream): no allocation or
-    // free of this workspace waits for other streams' kernels (a persistent serving kernel)
-    bool stream_ordered = false;
-    void* alloc_stream = nullptr;
     // host e2e staging
     void* dq = nullptr;
     void* did = nullptr;

@@ -15,37 +15,19 @@ int pow2_at_least(int v) {
 
 }  // namespace
 
-namespace {
-
-template <class T>
-cudaError_t ws_alloc(const Workspace& ws, T** p, size_t bytes) {
-    return ws.stream_ordered ? (cudaError_t)ordered_alloc(reinterpret_cast<void**>(p), bytes, ws.alloc_stream)
-                             : cudaMalloc(reinterpret_cast<void**>(p), bytes);
-}
-
-void ws_free(const Workspace& ws, void* p) {
-    if (!p) return;
-    if (ws.stream_ordered)
-        cudaFreeAsync(p, static_cast<cudaStream_t>(ws.alloc_stream));
-    else
-        cudaFree(p);
-}
-
-}  // namespace
-
 int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::string* why) {
     cudaError_t e;
     if (!ws.counters) {
-        if ((e = ws_alloc(ws, &ws.counters, 4 * sizeof(int32_t))) != cudaSuccess) return *why = "counters", (int)e;
+        if ((e = cudaMalloc(&ws.counters, 4 * sizeof(int32_t))) != cudaSuccess) return *why = "counters", (int)e;
     }
     if (ws.cap_q < nq) {
-        ws_free(ws, ws.overflow);
+        cudaFree(ws.overflow);
         ws.overflow = nullptr;
         ws.cap_q = 0;
-        ws_free(ws, ws.route);
+        cudaFree(ws.route);
         ws.route = nullptr;
-        if ((e = ws_alloc(ws, &ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess ||
-            (e = ws_alloc(ws, &ws.route, sizeof(int32_t) * (4 * nq + 2))) != cudaSuccess)
+        if ((e = cudaMalloc(&ws.overflow, sizeof(int32_t) * nq)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.route, sizeof(int32_t) * (4 * nq + 2))) != cudaSuccess)
             return *why = "overflow list", (int)e;
         ws.cap_q = nq;
     }
@@ -62,14 +44,12 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
         const int64_t pper = words * 4 + 8 * (ix.n + 1);
         int64_t pslots = std::max<int64_t>(kWarpsPerBlock, std::min<int64_t>(64, (1ll << 30) / pper));
         pslots = pslots / kWarpsPerBlock * kWarpsPerBlock;
-        const size_t bm_bytes = sizeof(uint32_t) * words * slots;
-        if ((e = ws_alloc(ws, &ws.bitmaps, bm_bytes)) != cudaSuccess ||
-            (e = ws_alloc(ws, &ws.backs, sizeof(uint64_t) * kBackPool * slots)) != cudaSuccess ||
-            (e = ws_alloc(ws, &ws.touched, sizeof(int32_t) * kTouchCap * slots)) != cudaSuccess ||
-            (e = ws.stream_ordered ? cudaMemsetAsync(ws.bitmaps, 0, bm_bytes, static_cast<cudaStream_t>(ws.alloc_stream))
-                                   : cudaMemset(ws.bitmaps, 0, bm_bytes)) != cudaSuccess ||
-            (e = ws_alloc(ws, &ws.pbitmaps, sizeof(uint32_t) * words * pslots)) != cudaSuccess ||
-            (e = ws_alloc(ws, &ws.pbacks, sizeof(uint64_t) * (ix.n + 1) * pslots)) != cudaSuccess) {
+        if ((e = cudaMalloc(&ws.bitmaps, sizeof(uint32_t) * words * slots)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.backs, sizeof(uint64_t) * kBackPool * slots)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.touched, sizeof(int32_t) * kTouchCap * slots)) != cudaSuccess ||
+            (e = cudaMemset(ws.bitmaps, 0, sizeof(uint32_t) * words * slots)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.pbitmaps, sizeof(uint32_t) * words * pslots)) != cudaSuccess ||
+            (e = cudaMalloc(&ws.pbacks, sizeof(uint64_t) * (ix.n + 1) * pslots)) != cudaSuccess) {
             workspace_free(ws);
             return *why = "device-memory search state", (int)e;
         }
@@ -82,14 +62,18 @@ int workspace_reserve(Workspace& ws, const DeviceIndex& ix, int64_t nq, std::str
 }
 
 void workspace_free(Workspace& ws) {
-    for (void* p : {(void*)ws.counters, (void*)ws.overflow, (void*)ws.route, (void*)ws.bitmaps, (void*)ws.backs,
-                    (void*)ws.touched, (void*)ws.pbitmaps, (void*)ws.pbacks, ws.dq, ws.did, ws.dd})
-        ws_free(ws, p);
-    const bool ordered = ws.stream_ordered;
-    void* st = ws.alloc_stream;
+    cudaFree(ws.counters);
+    cudaFree(ws.overflow);
+    cudaFree(ws.route);
+    cudaFree(ws.bitmaps);
+    cudaFree(ws.backs);
+    cudaFree(ws.touched);
+    cudaFree(ws.pbitmaps);
+    cudaFree(ws.pbacks);
+    cudaFree(ws.dq);
+    cudaFree(ws.did);
+    cudaFree(ws.dd);
     ws = Workspace{};
-    ws.stream_ordered = ordered;
-    ws.alloc_stream = st;
 }
 
 int launch_search(const SearchArgs& a, Workspace& ws, deg_stream_t stream, std::string* why) {

@@ -367,15 +367,6 @@ inline __device__ float exact_d2_lane(const float* x32, int32_t dim_pad, int32_t
     return a;
 }
 
-// One adjacency entry {internal id, caller id} as a single 64-bit relaxed load at GPU scope: the
-// serving kernel runs while deg_refine_live rewrites rows, so an entry must never be half old and
-// half new, and a row must not be served from a stale L1 line for the life of the kernel.
-__device__ __forceinline__ int2 load_adj_live(const int2* p) {
-    unsigned long long v;
-    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p));
-    return make_int2((int32_t)(uint32_t)(v & 0xffffffffull), (int32_t)(uint32_t)(v >> 32));
-}
-
 // Test-and-set of vertex id in C: 1 if it was not checked yet.
 __device__ __forceinline__ int visit(uint32_t* bm, int32_t id) {
     const uint32_t bit = 1u << (id & 31);
@@ -1030,8 +1021,7 @@ __device__ bool run_query(const Params& P, WarpState& W, int q, float* qv_smem, 
         int cnt = 0;
         for (int j0 = 0; j0 < P.degree; j0 += 32) {
             const int j = j0 + lane;
-            const int2* ep = P.adj + (int64_t)s * P.deg_pad + j;
-            const int2 e = j >= P.degree ? make_int2(-1, -1) : Mode == 2 ? load_adj_live(ep) : __ldg(ep);
+            const int2 e = j < P.degree ? __ldg(P.adj + (int64_t)s * P.deg_pad + j) : make_int2(-1, -1);
             const int32_t nb = e.x;
             if (nb >= 0 && P.row_bytes <= DEG_SEARCH_ROW_PREFETCH_BYTES) {
                 // start pulling the row into L2 while the visited test is in flight (a visited
@@ -1423,37 +1413,9 @@ int dispatch_shape(Params P, cudaStream_t st, void* t0, void* t1, std::string* w
     return (int)cudaErrorInvalidValue;
 }
 
-// Loads the batch-search kernels that dispatch_shape picks for rows of nchunk 16-byte chunks (both
-// front modes and the second kernel). With lazy module loading (the CUDA default) a kernel is
-// loaded at its first launch, and a load can wait for every kernel running on the device; a
-// persistent serving kernel then holds it up until it ends.
-template <class Rows, int G, int CPL>
-int preload_typed() {
-    cudaFuncAttributes fa;
-    cudaError_t e;
-    if ((e = cudaFuncGetAttributes(&fa, search_fast_kernel<Rows, G, CPL, 0>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa, search_fast_kernel<Rows, G, CPL, 1>)) != cudaSuccess ||
-        (e = cudaFuncGetAttributes(&fa, search_device_kernel<Rows, G, CPL>)) != cudaSuccess)
-        return (int)e;
-    return 0;
-}
-
-template <class Rows>
-int preload_shape(int nc) {
-    if (nc <= 4) return preload_typed<Rows, 4, 1>();
-    if (nc <= 8) return preload_typed<Rows, 8, 1>();
-    if (nc <= 16) return preload_typed<Rows, 16, 1>();
-    if (nc <= 32) return preload_typed<Rows, 32, 1>();
-    if (nc <= 64) return preload_typed<Rows, 32, 2>();
-    if (nc <= 128) return preload_typed<Rows, 32, 4>();
-    if (nc <= 256) return preload_typed<Rows, 32, 8>();
-    return (int)cudaErrorInvalidValue;
-}
-
 // The launchers, one translation unit per row format (search_f32.cu, search_bf16.cu, search_fp8.cu),
 // so the kernels of the three formats compile in parallel.
 int dispatch_search_f32(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
-int preload_search_f32(int nchunk);
 int dispatch_search_bf16(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
 int dispatch_search_fp8(Params P, cudaStream_t st, void* t0, void* t1, std::string* why);
 int dispatch_serve_f32(Params P, const ServeRing& S, const int32_t* pivots, int np, cudaStream_t st, int* warps,

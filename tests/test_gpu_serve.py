@@ -86,3 +86,18 @@ def test_full_ring_rejects_a_post(index):
     assert 5 not in got[s1][0]                              # exploration never returns its vertex
     srv.submit(vec=base[1], k=10, eps=0.1)                  # the ring has room again
     srv.stop()
+
+
+def test_max_blocks_caps_the_kernel(index):
+    # a server limited to 16 blocks keeps 16 x 4 warps and still answers, leaving the rest of the GPU
+    deg, idx, _ = index
+    q, vertices, ks, epss = _requests(64, 12)
+    srv = deg.Server(idx, capacity=256, kmax=128, idle_timeout_s=30.0, max_blocks=16)
+    assert srv.slots == 16 * 4
+    lat, ids, dists, st = srv.run_trace(q, vertices, ks, epss, np.zeros(len(ks)))
+    srv.stop()
+    assert (st == 0).all()
+    a_ids, a_d = idx.search(torch.from_numpy(q[:1]).cuda(), k=int(ks[0]), eps=float(epss[0])) if vertices[0] < 0 else \
+        idx.search(seeds=torch.tensor([vertices[0]], dtype=torch.int32, device="cuda"), explore=True, k=int(ks[0]),
+                   eps=float(epss[0]))
+    assert np.array_equal(ids[0, :int(ks[0])], a_ids.cpu().numpy()[0])

@@ -392,11 +392,10 @@ DEG_API deg_status knn_exact_noalloc(const float* base_dev, int64_t n, const flo
  * index in [0, n) of the nearest of rows_dev [n][dim] (float32, row-major), 1 <= n <= 4096, and
  * its float32 distance. This is the search the pivot entry routing runs (entry_mode 1). Results
  * are exact: the same float32 distances as knn_exact, ties to the lower index. Distances come
- * from one pass of bfloat16 tensor-core products reduced to the minimum of each group of 16 rows;
- * every group whose minimum lies within a proven rounding bound of the smallest is re-scored
- * exactly. `cap` (a power of two, 1 ... 4096) bounds the rows re-scored per query. A query with
- * more rows in such groups is scored exactly against all n rows instead, with the same result.
- * Allocates its scratch and synchronises the stream. DEG_EINVAL when n is
+ * from bfloat16 tensor-core products, and every row within a proven rounding bound of the
+ * smallest is re-scored exactly. `cap` (a power of two, 1 ... 4096) bounds the rows re-scored per
+ * query. A query with more rows inside the bound is scored exactly against all n rows instead,
+ * with the same result. Allocates its scratch and synchronises the stream. DEG_EINVAL when n is
  * outside 1 ... 4096, dim is not positive, nq is negative or above 2^24, a pointer is NULL, or
  * cap is not a power of two in 1 ... 4096; DEG_ECUDA on a device error. nq = 0 does nothing. */
 DEG_API deg_status deg_nearest_rows(const float* rows_dev, int64_t n, int32_t dim, const float* queries_dev, int64_t nq,

@@ -650,14 +650,22 @@ __global__ void __launch_bounds__(kRerankThreads) rerank_kernel(const RerankArgs
 }
 
 // k = 1, one warp per query: limit = window_limit(min of the group minima, b_q).
-// k = 1, one warp per query, straight from the group minima of the approximate pass (over every
-// row): with m the smallest group minimum (the smallest approximate distance a of any row), the
-// nearest row x* has a(x*) <= e(x*) + b <= m + 2b, so its group's minimum is within the limit, and
-// so is that of every row tied with it. The rows of the groups within the limit are scored exactly
-// (float32, dimension order) and the smallest (distance, row) wins; if those are more than `cap`
-// rows, every row is scored instead (the same answer).
-__global__ void nearest_groups_kernel(const float* __restrict__ gmin, int ng, int cap, const float* __restrict__ qn,
-                                      const float* __restrict__ rq, const float* __restrict__ maxima, int32_t kpad,
+__global__ void nearest_limit_kernel(const float* __restrict__ gmin, int ng, int64_t nq, const float* __restrict__ qn,
+                                     const float* __restrict__ rq, const float* __restrict__ maxima, int32_t kpad,
+                                     float* __restrict__ limit) {
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= nq) return;
+    float m = __int_as_float(0x7f800000);
+    for (int i = lane; i < ng; i += 32) m = fminf(m, gmin[q * ng + i]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) limit[q] = window_limit(m, error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
+}
+
+// k = 1, one warp per query: the exact (distance, row) minimum over the candidates, or over every
+// row when they overflowed. All candidates are scored, so no selection is needed.
+__global__ void nearest_finish_kernel(const unsigned long long* __restrict__ cand, const int32_t* __restrict__ cnt, int cap,
                                       const float* __restrict__ qf, const float* __restrict__ xf, int32_t dim, int64_t n,
                                       int64_t nq, int32_t* __restrict__ ids, float* __restrict__ dists,
                                       const int32_t* __restrict__ error) {
@@ -671,37 +679,18 @@ __global__ void nearest_groups_kernel(const float* __restrict__ gmin, int ng, in
         }
         return;
     }
-    const float* g = gmin + q * ng;
-    float m = __int_as_float(0x7f800000);
-    for (int i = lane; i < ng; i += 32) m = fminf(m, g[i]);
-#pragma unroll
-    for (int o = 16; o; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const float lim = window_limit(m, error_bound(qn[q], rq[q], maxima[0], maxima[1], kpad));
-    int groups = 0;
-    for (int i0 = 0; i0 < ng; i0 += 32) groups += __popc(__ballot_sync(0xffffffffu, i0 + lane < ng && g[i0 + lane] <= lim));
     const float* qv = qf + q * dim;
     const bool vec = (dim & 3) == 0 && (reinterpret_cast<uintptr_t>(xf) & 15) == 0 && (reinterpret_cast<uintptr_t>(qf) & 15) == 0;
+    const int c = cnt[q];
     unsigned long long best = ~0ull;
-    if ((int64_t)groups * 16 > cap) {
+    if (c <= cap) {
+        for (int i = lane; i < c; i += 32) {
+            const uint32_t x = (uint32_t)cand[q * cap + i];
+            best = min(best, ((unsigned long long)__float_as_uint(exact_row_d2(qv, xf, x, dim, vec)) << 32) | x);
+        }
+    } else {
         for (int64_t x = lane; x < n; x += 32)
             best = min(best, ((unsigned long long)__float_as_uint(exact_row_d2(qv, xf, x, dim, vec)) << 32) | (uint32_t)x);
-    } else {
-        for (int i0 = 0; i0 < ng; i0 += 32) {
-            unsigned want = __ballot_sync(0xffffffffu, i0 + lane < ng && g[i0 + lane] <= lim);
-            while (want) {                                   // two groups at a time, 16 lanes each
-                const int ga = __ffs(want) - 1;
-                want &= want - 1;
-                int gb = -1;
-                if (want) {
-                    gb = __ffs(want) - 1;
-                    want &= want - 1;
-                }
-                const int mine = lane < 16 ? ga : gb;
-                const int64_t x = (int64_t)(i0 + mine) * 16 + (lane & 15);
-                if (mine >= 0 && x < n)
-                    best = min(best, ((unsigned long long)__float_as_uint(exact_row_d2(qv, xf, x, dim, vec)) << 32) | (uint32_t)x);
-            }
-        }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
@@ -1065,15 +1054,17 @@ int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, flo
     const TcArgs fa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, nullptr, p->limit, p->cand, p->cnt,
                     p->cap, p->flags};
     dist_tc_kernel<false><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, sa);
-    if (p->k == 1) {
-        // the group minima cover every row: the groups within the bound are re-scored directly
-        const unsigned wblocks = (unsigned)((nq + 7) / 8);   // one warp per query, 8 per block
-        nearest_groups_kernel<<<wblocks, 256, 0, st>>>(p->gmin, (int)p->ng, p->cap, p->qn, p->qr, p->maxima, p->kpad, queries,
-                                                       p->x32, p->dim, p->n, nq, ids, dists ? dists : p->dscr, p->flags);
-    } else {
+    const unsigned wblocks = (unsigned)((nq + 7) / 8);   // one warp per query, 8 per block
+    if (p->k == 1)
+        nearest_limit_kernel<<<wblocks, 256, 0, st>>>(p->gmin, (int)p->ng, nq, p->qn, p->qr, p->maxima, p->kpad, p->limit);
+    else
         sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng, p->k, p->qn, p->qr, p->maxima, p->kpad,
                                                                   p->limit);
-        dist_tc_kernel<true><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, fa);
+    dist_tc_kernel<true><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, fa);
+    if (p->k == 1) {
+        nearest_finish_kernel<<<wblocks, 256, 0, st>>>(p->cand, p->cnt, p->cap, queries, p->x32, p->dim, p->n, nq, ids,
+                                                       dists ? dists : p->dscr, p->flags);
+    } else {
         const RerankArgs ra{p->cand, p->cnt, p->cap, p->k, queries, p->x32, p->dim, p->qn, p->qr, p->maxima, p->kpad,
                             ids, dists ? dists : p->dscr, p->flags + 1, (int32_t)p->n, p->flags};
         rerank_kernel<<<(unsigned)nq, kRerankThreads, p->rerank_smem, st>>>(ra);

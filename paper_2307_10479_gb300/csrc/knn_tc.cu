@@ -936,11 +936,6 @@ struct KnnPlan {
     int64_t n = 0;
     int32_t dim = 0, kpad = 0, k = 0, cap = 0, sms = 0, rerank_smem = 0;
     int64_t tiles = 0, ng = 0;
-    // the sample pass of k = 1 plans: every sstride-th row (one 256-row tile of them), its norms xs
-    // and tensor map tx_s; for k > 1 the sample is every row (xs = xn, tx_s = tx)
-    int64_t sstride = 1, ns = 0, tiles_s = 0, ng_s = 0;
-    float* xs = nullptr;
-    CUtensorMap tx_s;
     float* x32 = nullptr;             // [n][dim] contiguous float32 rows
     __nv_bfloat16* xb = nullptr;      // [n][kpad]
     float* xn = nullptr;              // [tiles * 256], zero padded
@@ -976,7 +971,6 @@ void plan_free_scratch(KnnPlan* p) {
 void knn_plan_destroy(KnnPlan* p) {
     if (!p) return;
     plan_free_scratch(p);
-    if (p->xs != p->xn) cudaFree(p->xs);
     cudaFree(p->x32);
     cudaFree(p->xb);
     cudaFree(p->xn);
@@ -999,13 +993,6 @@ int knn_plan_create(KnnPlan** out, const float* rows, int64_t row_stride, const 
     p->cap = cap;
     p->tiles = (n + TN - 1) / TN;
     p->ng = (n + 15) / 16;
-    // k = 1: the threshold comes from a sample of at most one tile of rows (its minimum is at least
-    // the minimum over all rows, so the candidates still hold every nearest row); the filter pass
-    // then finds the ~sstride rows below it
-    p->sstride = k == 1 ? std::max<int64_t>(1, (n + TN - 1) / TN) : 1;
-    p->ns = (n + p->sstride - 1) / p->sstride;
-    p->tiles_s = (p->ns + TN - 1) / TN;
-    p->ng_s = (p->ns + 15) / 16;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1017,20 +1004,12 @@ int knn_plan_create(KnnPlan** out, const float* rows, int64_t row_stride, const 
         knn_plan_destroy(p);
         return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
     }
-    if (p->sstride == 1) {
-        p->xs = p->xn;
-    } else if ((e = cudaMalloc(&p->xs, 4ull * p->tiles_s * TN)) != cudaSuccess) {
-        knn_plan_destroy(p);
-        return *why = std::string("knn plan: ") + cudaGetErrorString(e), (int)e;
-    }
     cudaMemsetAsync(p->xn, 0, 4ull * p->tiles * TN, st);
     cudaMemsetAsync(p->maxima, 0, 16, st);
     gather_plan_rows_kernel<<<256, 256, 0, st>>>(rows, row_stride, row_ids, n, dim, p->x32);
     bf16_rows_kernel<<<256, 256, 0, st>>>(p->x32, n, dim, p->kpad, p->xb, p->xn, p->xr);
     row_maxima_kernel<<<64, 256, 0, st>>>(p->xn, p->xr, n, p->maxima);
-    if (p->sstride > 1) strided_norms_kernel<<<16, 256, 0, st>>>(p->xn, p->sstride, p->ns, p->tiles_s * TN, p->xs);
-    if (!make_map(&p->tx, p->xb, n, p->kpad, 2ull * p->kpad, TN) ||
-        !make_map(&p->tx_s, p->xb, p->ns, p->kpad, 2ull * p->kpad * p->sstride, TN)) {
+    if (!make_map(&p->tx, p->xb, n, p->kpad, 2ull * p->kpad, TN)) {
         knn_plan_destroy(p);
         return *why = "knn plan: tensor map encoding failed", (int)cudaErrorInvalidValue;
     }
@@ -1070,17 +1049,16 @@ int knn_plan_run(KnnPlan* p, const float* queries, int64_t nq, int32_t* ids, flo
     cudaMemsetAsync(p->flags, 0, 16, st);
     cudaMemsetAsync(p->cnt, 0, 4ull * nq, st);
     bf16_rows_kernel<<<256, 256, 0, st>>>(queries, nq, p->dim, p->kpad, p->qb, p->qn, p->qr);
-    const TcArgs sa{0, (int32_t)nq, qblocks, p->ns, p->tiles_s, p->kpad / KC, p->qn, p->xs, p->gmin, nullptr, nullptr, nullptr,
-                    0, p->flags};
+    const TcArgs sa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, p->gmin, nullptr, nullptr, nullptr, 0,
+                    p->flags};
     const TcArgs fa{0, (int32_t)nq, qblocks, p->n, p->tiles, p->kpad / KC, p->qn, p->xn, nullptr, p->limit, p->cand, p->cnt,
                     p->cap, p->flags};
-    const unsigned grid_s = (unsigned)std::min<int64_t>((int64_t)qblocks * p->tiles_s, p->sms);
-    dist_tc_kernel<false><<<grid_s, kTcThreads, kSmemDyn, st>>>(tq, p->tx_s, sa);
+    dist_tc_kernel<false><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, sa);
     const unsigned wblocks = (unsigned)((nq + 7) / 8);   // one warp per query, 8 per block
     if (p->k == 1)
-        nearest_limit_kernel<<<wblocks, 256, 0, st>>>(p->gmin, (int)p->ng_s, nq, p->qn, p->qr, p->maxima, p->kpad, p->limit);
+        nearest_limit_kernel<<<wblocks, 256, 0, st>>>(p->gmin, (int)p->ng, nq, p->qn, p->qr, p->maxima, p->kpad, p->limit);
     else
-        sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng_s, p->k, p->qn, p->qr, p->maxima, p->kpad,
+        sample_limit_kernel<<<(unsigned)nq, kSelThreads, 0, st>>>(p->gmin, (int)p->ng, p->k, p->qn, p->qr, p->maxima, p->kpad,
                                                                   p->limit);
     dist_tc_kernel<true><<<grid, kTcThreads, kSmemDyn, st>>>(tq, p->tx, fa);
     if (p->k == 1) {

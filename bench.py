@@ -438,7 +438,11 @@ def serving(deg, idx, w, q, gt):
                                        # the rate the slots sustain when every one is busy: slots over
                                        # the mean device time of a request of this mix
                                        "device_mean_ms": 1e3 * float(np.mean(dev)),
-                                       "slots_ceiling_qps": srv.slots / float(np.mean(dev))}
+                                       "slots_ceiling_qps": srv.slots / float(np.mean(dev)),
+                                       # sustained = requests / wall: the arrivals span arrival_s, and
+                                       # the last requests still finish after it (drain_ms)
+                                       "arrival_s": float(arrivals[-1]),
+                                       "drain_ms": 1e3 * (wall - float(arrivals[-1]))}
             log(f"[bench] serving {rate}/s: sustained {n / wall:.0f}/s, p50 {1e3 * np.median(lat):.2f} ms, "
                 f"p99 {1e3 * np.percentile(lat, 99):.2f} ms, recall@10 {rec:.4f}")
     finally:

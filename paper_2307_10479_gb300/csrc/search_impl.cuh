@@ -120,18 +120,39 @@ __device__ __forceinline__ uint64_t warp_min64(uint64_t v) {
 // ---- row storage formats ------------------------------------------------------------------
 // A row is read as 16-byte chunks; each chunk holds EPC elements.
 // Row formats. acc() folds one 16-byte chunk of a row into a lane's two partial sums (two
-// independent FMA chains) and fin() turns the warp-reduced sum into the squared distance: float32 and bf16 rows sum (q - x)^2 directly; FP8 rows
-// sum q . x and expand ||q - s x||^2 = ||q||^2 - 2 s (q . x) + s^2 ||x||^2 with the row's s and
-// s^2 ||x||^2 read from one float2 (one FMA per element instead of two).
+// independent FMA chains, even and odd elements, advanced together by paired float32
+// instructions) and fin() turns the warp-reduced sum into the squared distance: float32 and bf16
+// rows sum (q - x)^2 directly; FP8 rows sum q . x and expand ||q - s x||^2 = ||q||^2 - 2 s (q . x) +
+// s^2 ||x||^2 with the row's s and s^2 ||x||^2 read from one float2 (one FMA per element instead
+// of two).
+
+// (a0, a1) += (x0, x1) * (y0, y1), and (a0, a1) += ((q0, q1) - (x0, x1))^2, each step one paired
+// (.f32x2) instruction: per lane the same IEEE fma and subtraction as the scalar forms, so the sums
+// are bit-identical to fmaf chains.
+__device__ __forceinline__ void fma_pair(float& a0, float& a1, float x0, float x1, float y0, float y1) {
+    unsigned long long a, x, y;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(y0), "f"(y1));
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(a) : "l"(x), "l"(y));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
+}
+__device__ __forceinline__ void sub_sq_pair(float& a0, float& a1, float q0, float q1, float x0, float x1) {
+    unsigned long long a, q, x, t;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(q) : "f"(q0), "f"(q1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(q), "l"(x));
+    asm("fma.rn.f32x2 %0, %1, %1, %0;" : "+l"(a) : "l"(t));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a0), "=f"(a1) : "l"(a));
+}
+
 struct F32Rows {
     static constexpr int EPC = 4;
     __device__ static float2 scale(const float2*, int32_t) { return make_float2(1.f, 0.f); }
     __device__ static void acc(const uint4& c, const float* q, float& a0, float& a1) {
-        float t;
-        t = q[0] - __uint_as_float(c.x); a0 = fmaf(t, t, a0);
-        t = q[1] - __uint_as_float(c.y); a1 = fmaf(t, t, a1);
-        t = q[2] - __uint_as_float(c.z); a0 = fmaf(t, t, a0);
-        t = q[3] - __uint_as_float(c.w); a1 = fmaf(t, t, a1);
+        sub_sq_pair(a0, a1, q[0], q[1], __uint_as_float(c.x), __uint_as_float(c.y));
+        sub_sq_pair(a0, a1, q[2], q[3], __uint_as_float(c.z), __uint_as_float(c.w));
     }
     __device__ static float fin(float a, float2, float) { return a; }
 };
@@ -141,12 +162,8 @@ struct BF16Rows {
     __device__ static void acc(const uint4& c, const float* q, float& a0, float& a1) {
         const uint32_t w[4] = {c.x, c.y, c.z, c.w};
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            float t = q[2 * i] - __uint_as_float(w[i] << 16);          // bf16 -> f32 is exact
-            a0 = fmaf(t, t, a0);
-            t = q[2 * i + 1] - __uint_as_float(w[i] & 0xffff0000u);
-            a1 = fmaf(t, t, a1);
-        }
+        for (int i = 0; i < 4; ++i)
+            sub_sq_pair(a0, a1, q[2 * i], q[2 * i + 1], __uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xffff0000u));
     }
     __device__ static float fin(float a, float2, float) { return a; }
 };
@@ -162,8 +179,7 @@ struct FP8Rows {
                 const __nv_fp8x2_storage_t pair = (__nv_fp8x2_storage_t)((w[i] >> (16 * h)) & 0xffffu);
                 const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(pair, __NV_E4M3);  // exact
                 const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
-                a0 = fmaf(q[4 * i + 2 * h], f.x, a0);
-                a1 = fmaf(q[4 * i + 2 * h + 1], f.y, a1);
+                fma_pair(a0, a1, q[4 * i + 2 * h], q[4 * i + 2 * h + 1], f.x, f.y);
             }
         }
     }

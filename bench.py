@@ -399,7 +399,8 @@ def run_stop_sweep(args):
 
 
 SERVE_RATES = (50_000, 100_000, 200_000, 500_000)
-SERVE_REQUESTS = 100_000
+SERVE_REQUESTS = 100_000        # at least this many requests per rate
+SERVE_SECONDS = 2.0             # and at least this long an arrival window (1,000,000 requests at 500k/s)
 
 
 def serving(deg, idx, w, q, gt):
@@ -408,12 +409,13 @@ def serving(deg, idx, w, q, gt):
     Reports p50/p99 latency (arrival to completion seen by the host), sustained QPS and recall@10
     of the vector requests with k >= 10."""
     rng = np.random.default_rng(4)
-    out = {"index": "bf16 rows + re-rank, pivot entry", "requests_per_rate": SERVE_REQUESTS, "rates": {}}
+    out = {"index": "bf16 rows + re-rank, pivot entry", "requests_per_rate": {str(r): max(SERVE_REQUESTS, int(SERVE_SECONDS * r))
+                                                                           for r in SERVE_RATES}, "rates": {}}
     srv = deg.Server(idx, capacity=1 << 16, kmax=100, precision="bf16", entry="pivot", idle_timeout_s=60.0)
     out["slots"] = srv.slots
     try:
         for rate in SERVE_RATES:
-            n = SERVE_REQUESTS
+            n = max(SERVE_REQUESTS, int(SERVE_SECONDS * rate))
             ks = rng.choice([1, 10, 100], n).astype(np.int32)
             epss = rng.choice([0.05, 0.1, 0.2], n).astype(np.float32)
             explore = rng.random(n) < 0.2

@@ -318,7 +318,14 @@ typedef struct {
                                 many, leaving the rest of the GPU to other kernels                  */
 } deg_serve_config;
 
-/* Launch the serving kernel on its own stream. The index must stay alive until deg_serve_stop. */
+/* Launch the serving kernel on its own (non-blocking) stream. The index must stay alive, and must
+ * not be uploaded again or freed, until deg_serve_stop. The request ring (vectors, parameters,
+ * results) lives in mapped pinned host memory owned by the server. *out is NULL on any error:
+ * DEG_EINVAL for a NULL argument or a bad config (capacity < 1, kmax outside 1..1024,
+ * idle_timeout_s <= 0, entry_mode outside 0..2, rerank outside 0..1024, max_blocks < 0);
+ * DEG_ENOTREADY if the index, or its copy in the chosen precision, is not uploaded, or if
+ * learned_stop is set without a stop model; DEG_ENOMEM / DEG_ECUDA if an allocation or the launch
+ * fails (entry_mode 2 without learned entry points is a launch failure). */
 DEG_API deg_status deg_serve_start(deg_index* idx, const deg_serve_config* cfg, deg_server** out);
 
 /* Post one request: vec_host [dim] float32 for a vector query (vertex = -1), or vec_host NULL
